@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Throughput of the pseudo-spectral forced-HIT + passive-scalar time step.
+
+Default workload: N = 1024^3, FP32-mixed (FP32 transforms and products, FP64
+reductions and integrating-factor exponentials), constant-power forcing
+eps = 0.1 on |k| <= 2, Sc = 1 scalar with a unit mean gradient, CFL 0.5 with
+dt reset every 10 steps, statistics records (spectra, dissipation,
+gradient skewness/flatness) every 10 steps.  One "step" is one RK4 step (four
+right-hand-side evaluations and stage updates) plus its share of the records.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# 1024^3 workload (nu from k_max eta = 1.5 with k_max = N/3 at eps = 0.1)
+WORKLOAD = dict(N=1024, nu=3.341e-4, Sc=1.0, beta=1.0, kF=2.0, eps_inj=0.1, cfl=0.5,
+                seed=3, ic_energy=1.5, record_every=10)
+ORACLE_SAMPLE_N = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=WORKLOAD["N"])
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed FP64 companion steps (0 = skip)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+
+def kernel_bytes(N: int, cbytes: int) -> dict:
+    """Algorithmic bytes per launch of each kernel kind (reads + writes of the
+    minimum data each pass must move; complex elements of `cbytes` bytes)."""
+    K = (N - 1) // 3
+    M, P = K + 1, 2 * K + 1
+    S, zs, ys = P * P * M, N * P * M, N * N * M
+    return {
+        "zinv": (4 * S + 7 * zs) * cbytes,
+        "yinv": (7 * zs + 9 * ys) * cbytes,
+        "xpass": (9 * ys + 4 * ys) * cbytes,
+        "yfwd": (4 * ys + 4 * zs) * cbytes,
+        "zfwd": (4 * zs + 4 * S) * cbytes,
+        # stage updates: 16 S (stages 1, 4) and 24 S (stages 2, 3) complex values
+        "combine": 20 * S * cbytes,
+    }
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.p = None
+        self.path = os.path.join("/tmp", f"psc_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def oracle_steps_per_s(nsteps: int = 2, N: int = ORACLE_SAMPLE_N):
+    """FP64 oracle RK4 steps/s on this host at N^3 (single thread NumPy)."""
+    from oracle import psc_oracle as O
+    p = O.Params(N=N, nu=WORKLOAD["nu"] * WORKLOAD["N"] / N, Sc=1.0, beta=1.0, kF=2.0, eps_inj=0.1,
+                 cfl=0.5, seed=3, ic=O.IC_SPECTRUM_K4, ic_energy=1.5)
+    g = O.Grid(N)
+    uh, ph = O.init_field(g, p)
+    dt = O.cfl_dt(uh, g, p.cfl)
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        uh, ph = O.step(uh, ph, g, p, dt)
+    el = time.perf_counter() - t0
+    return nsteps / el, el
+
+
+def oracle_scale(N_from: int, N_to: int) -> float:
+    """Work ratio of one step at N_to vs N_from: N^3 log2 N."""
+    return (N_to ** 3 * math.log2(N_to)) / (N_from ** 3 * math.log2(N_from))
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import psc_oracle as O
+    N = ORACLE_SAMPLE_N
+    p = O.Params(N=N, nu=WORKLOAD["nu"] * WORKLOAD["N"] / N, Sc=1.0, beta=1.0, kF=2.0, eps_inj=0.1,
+                 cfl=0.5, seed=3, ic=O.IC_SPECTRUM_K4, ic_energy=1.5)
+    g = O.Grid(N)
+    uh, ph = O.init_field(g, p)
+    dt = O.cfl_dt(uh, g, p.cfl)
+    for _ in range(a.warmup):
+        uh, ph = O.step(uh, ph, g, p, dt)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        uh, ph = O.step(uh, ph, g, p, dt)
+    el = time.perf_counter() - t0
+    scale = oracle_scale(N, a.N)
+    val = a.steps / el / scale
+    sample = (f"each step = one FP64 oracle RK4 step at {N}^3 (NumPy, 1 thread), scaled to {a.N}^3 "
+              f"by N^3 log2 N (x{scale:.1f})")
+    out = {"impl": "reference", "metric": "RK4 steps/s", "value": val, "unit": "steps/s",
+           "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+           "ms_per_step": 1000.0 / val, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{a.N}^3 forced HIT + passive scalar (oracle sample at {N}^3)",
+                      "N": a.N, "sample_N": N},
+           "cpu_baseline": {"value": val, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": val, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2012_04838_gb300 as psc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    N = a.N
+    prm = psc.Params(N=N, precision=psc.FP32_MIXED, nu=WORKLOAD["nu"] * WORKLOAD["N"] / N,
+                     Sc=WORKLOAD["Sc"], beta=WORKLOAD["beta"], kF=WORKLOAD["kF"],
+                     eps_inj=WORKLOAD["eps_inj"], cfl=WORKLOAD["cfl"], seed=WORKLOAD["seed"] + rank,
+                     ic=psc.IC_SPECTRUM_K4, ic_energy=WORKLOAD["ic_energy"],
+                     record_every=WORKLOAD["record_every"])
+    sim = psc.Simulation(prm, device=dev)
+    stream = sim.stream
+    sim.init_field()
+    rec_every = prm.record_every
+
+    def run_steps(n, start):
+        for i in range(n):
+            sim.step(1)
+            if (start + i) % rec_every == 0:
+                sim.stats()
+
+    run_steps(a.warmup, 0)
+    torch.cuda.synchronize()
+    sim.profile_read()  # discard warm-up timings
+    sim.profile(True)
+    n0 = sim.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        e0.record(stream)
+        run_steps(a.steps, 0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = sim.launch_count() - n0
+    prof = sim.profile_read()
+    sim.profile(False)
+    last_rec, _, _ = sim.stats()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * a.steps / (ms / 1000.0)
+
+    # roofline of the dominant kernel (per-launch device time from CUDA events)
+    kb = kernel_bytes(N, 8)
+    peak, peak_src = peaks()
+    kinds = {k: v for k, v in prof.items() if k in kb and v[1] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dms, dn = kinds[dom]
+    ach = kb[dom] / (dms / dn / 1000.0) / 1e9
+    per_kernel = {k: {"ms_total": round(v[0], 3), "launches": v[1],
+                      "ms_per_launch": round(v[0] / v[1], 4) if v[1] else None,
+                      "GBps": round(kb[k] / (v[0] / v[1] / 1000.0) / 1e9, 1) if (v[1] and k in kb) else None}
+                  for k, v in prof.items()}
+    step_bytes = 4 * sum(kb.values())
+    traffic = None
+    prof_file = os.path.join(ROOT, "profiles", f"traffic_{dom}_fp32_N{N}.json")
+    if os.path.exists(prof_file):
+        try:
+            with open(prof_file) as f:
+                tf = json.load(f)
+            if tf.get("kernel_digest") == _kernel_digest():
+                traffic = tf.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    out = {"metric": "RK4 steps/s", "value": value, "unit": "steps/s", "n_gpus": world,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": f"{N}^3 forced HIT + passive scalar, FP32-mixed "
+                                  "(FP64 reductions and IF exponentials), CFL 0.5, records every 10 steps",
+                      "N": N, "precision": "fp32_mixed", "nu": prm.nu, "Sc": prm.Sc, "kF": prm.kF,
+                      "eps_inj": prm.eps_inj, "record_every": rec_every,
+                      "l2": "inputs larger than L2 (state %.2f GB, working set %.1f GB)"
+                            % (sim.state_bytes() / 1e9, psc.workspace_size(prm) / 1e9),
+                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+           "grid_point_stages_per_s": value * 4 * N ** 3,
+           "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peak,
+                        "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": traffic,
+                        "algorithmic_bytes_per_launch": kb[dom], "peak_source": peak_src},
+           "step_roofline": {"algorithmic_bytes_per_step": step_bytes,
+                             "achieved_GBps": round(step_bytes / (ms / a.steps / 1000.0) / 1e9, 1),
+                             "frac": round(step_bytes / (ms / a.steps / 1000.0) / 1e9 / peak, 4)},
+           "kernels": per_kernel, "gpu_launches": launches, "clocks": clk.summary(),
+           "last_record": {k: last_rec[k] for k in ("t", "dt", "K", "eps", "Re_lambda", "kmax_eta", "cfl",
+                                                    "phi_var", "chi")}}
+
+    # end to end through the C ABI with host buffers: initial state in from
+    # pinned host memory, steps with records, final state back to pinned memory
+    if not a.no_e2e:
+        host = sim.get_state(device="cpu").pin_memory()
+        back = torch.empty_like(host).pin_memory()
+        nrec = 0
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        sim.set_state(host)
+        for i in range(a.steps):
+            sim.step(1)
+            if i % rec_every == 0:
+                sim.stats()
+                nrec += 1
+        st = sim.lib.psc_get_state(sim._h, back.data_ptr(), sim.state_bytes())
+        if st != 0:
+            raise RuntimeError("psc_get_state failed")
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        rec_bytes = 37 * 8 + 2 * 8 * 600
+        out["e2e"] = {"value": world * a.steps / el, "unit": "steps/s",
+                      "h2d_bytes_per_step": sim.state_bytes() / a.steps,
+                      "d2h_bytes_per_step": (sim.state_bytes() + nrec * rec_bytes) / a.steps,
+                      "what": "set_state from pinned host memory, steps with records every 10 steps, "
+                              "get_state to pinned host memory"}
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    # FP64 companion of the same workload ("mixed vs FP64")
+    if a.fp64_steps > 0:
+        p64 = psc.Params(**{**prm.__dict__, "precision": psc.FP64})
+        try:
+            s64 = psc.Simulation(p64, device=dev)
+            s64.init_field()
+            s64.step(1)
+            torch.cuda.synchronize()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(s64.stream)
+            s64.step(a.fp64_steps)
+            f1.record(s64.stream)
+            torch.cuda.synchronize()
+            fms = f0.elapsed_time(f1) / a.fp64_steps
+            out["fp64"] = {"steps_per_s": 1000.0 / fms, "ms_per_step": fms, "steps": a.fp64_steps,
+                           "mixed_over_fp64": value / (world * 1000.0 / fms)}
+            s64.close()
+            del s64
+            torch.cuda.empty_cache()
+        except Exception as e:  # report, do not hide
+            out["fp64"] = {"error": str(e)[:200]}
+
+    if rank == 0 and not a.no_cpu_baseline:
+        sps, el = oracle_steps_per_s(2)
+        sc = oracle_scale(ORACLE_SAMPLE_N, N)
+        out["cpu_baseline"] = {"value": sps / sc, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                               "sample": f"2 FP64 oracle RK4 steps at {ORACLE_SAMPLE_N}^3 "
+                                         f"({el:.1f} s, NumPy single thread), scaled to {N}^3 by "
+                                         f"N^3 log2 N (x{sc:.1f})"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def _kernel_digest() -> str:
+    """Digest of the kernel sources, to tell whether stored ncu counters still apply."""
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2012_04838_gb300", "csrc")
+    for n in sorted(os.listdir(d)):
+        if n.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, n), "rb").read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,178 @@
+/*
+ * psc.h -- C ABI of the GB300 pseudo-spectral solver for forced homogeneous
+ * isotropic turbulence with a passive scalar (arXiv:2012.04838, section 2).
+ *
+ * The library advances, on one GPU, the Fourier-Galerkin system of the paper:
+ *   d u_k/dt   = P_k (u x omega)_k - nu |k|^2 u_k + A u_k 1[0<|k|^2<=kF^2]   (Eqs. 6-7)
+ *   d phi_k/dt = -(u . grad phi)_k - beta u2_k - D |k|^2 phi_k, D = nu/Sc    (Eq. 8)
+ * on the periodic box [0, 2 pi]^3 with N^3 points (Eq. 4) and the DFT
+ * convention of Eq. 5 (forward unnormalised, inverse scaled by 1/N^3).
+ *
+ * Conventions shared by every entry point
+ *   - Status: every call returns psc_status; nothing is thrown across the ABI.
+ *     psc_last_error() gives a message for the last failing call.
+ *   - Memory: the caller owns all device memory.  psc_workspace_size() says how
+ *     many bytes of device memory one simulation needs; the caller allocates
+ *     them (for example with PyTorch) and passes the pointer to psc_create().
+ *     The library itself allocates no device memory.
+ *   - Streams: all device work of a simulation is enqueued on the CUDA stream
+ *     given to psc_create() (NULL = legacy default stream).  Calls that return
+ *     data to host memory synchronise that stream; the others are asynchronous.
+ *   - Threads: one simulation must not be used from two host threads at once;
+ *     distinct simulations are independent.
+ *   - Spectral layout ("compact state"): with K = floor((N-1)/3) (2/3 rule),
+ *     P = 2K+1 and M = K+1, the state is four fields (u1, u2, u3, phi), each
+ *     a [P][P][M] array of complex numbers (interleaved real, imaginary) with
+ *     element [kz+K][ky+K][kx] holding the unnormalised Fourier coefficient
+ *     of wavevector (kx, ky, kz), |kx|,|ky|,|kz| <= K, kx >= 0.  The kx = 0
+ *     plane is conjugate-symmetric (real fields); the k = 0 entry is zero.
+ *     Complex numbers are float pairs (PSC_FP32_MIXED) or double pairs (PSC_FP64).
+ */
+#ifndef PSC_H
+#define PSC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PSC_OK = 0,
+  PSC_EINVAL = 1,          /* invalid argument or parameter                      */
+  PSC_ENOMEM_BUDGET = 2,   /* workspace smaller than psc_workspace_size()         */
+  PSC_ECUDA = 3,           /* a CUDA runtime call failed (see psc_last_error)     */
+  PSC_EUNSTABLE = 4,       /* non-finite velocity seen by the CFL monitor (Eq. 10)*/
+  PSC_ETIMEOUT = 5,        /* reserved: a bounded device wait gave up             */
+  PSC_EUNSUPPORTED_N = 6   /* N outside the supported set of grid sizes           */
+} psc_status;
+
+typedef enum { PSC_FP64 = 0, PSC_FP32_MIXED = 1 } psc_precision;
+typedef enum { PSC_IC_SPECTRUM_K4 = 0, PSC_IC_TAYLOR_GREEN_NOISE = 1, PSC_IC_PAPER_EQ9 = 2 } psc_ic;
+typedef enum { PSC_FORCE_NONE = 0, PSC_FORCE_CONST_POWER = 1 } psc_forcing;
+typedef enum { PSC_INTEG_IFRK4 = 0, PSC_INTEG_RK4 = 1 } psc_integrator;
+
+/* Problem statement (Table 2 of the paper; Sc and beta from section 2.3).
+ * Fields are plain values; zero-initialise and set what you need. */
+typedef struct {
+  int32_t N;            /* grid points per side; box side 2 pi (section 3.1)          */
+  int32_t precision;    /* psc_precision                                              */
+  double nu;            /* kinematic viscosity (Eq. 1)                                */
+  double Sc;            /* Schmidt number, D = nu/Sc (section 2.3)                    */
+  double beta;          /* uniform mean scalar gradient along x2 (Eq. 3)              */
+  int32_t forcing;      /* psc_forcing                                                */
+  int32_t integrator;   /* psc_integrator: Lawson IF-RK4 or plain RK4 (section 2.2)   */
+  double kF;            /* forcing sphere 0 < |k| <= kF (section 2.3)                 */
+  double eps_inj;       /* injected power for PSC_FORCE_CONST_POWER                   */
+  double dt;            /* time step; used as is when cfl <= 0                        */
+  double cfl;           /* > 0: dt reset to reach this CFL (Eq. 10) at step 0 and at
+                           every record_every-th step, held in between                */
+  uint64_t seed;        /* initial-condition seed                                     */
+  int32_t ic;           /* psc_ic                                                     */
+  int32_t record_every; /* steps between CFL resets (>= 1)                            */
+  double ic_energy;     /* target K of the random IC (u_rms = 1 gives 1.5)            */
+  double ic_noise_frac; /* Taylor-Green IC: noise energy as a fraction of 1/8         */
+  int32_t scalar_on;    /* 0: phi is held at zero                                     */
+  int32_t reserved;
+} psc_params;
+
+/* One statistics record of the current state (section 2.3): Table 1,
+ * Eqs. 11-12 (velocity- and scalar-gradient skewness and flatness) and the
+ * terms of Eq. 13.  eps and chi come from the spectrum; eps_phys = nu <|omega|^2>
+ * and chi_phys = 2 D <|grad phi|^2> are grid averages (equal up to rounding). */
+typedef struct {
+  double t, dt;
+  double K, K_phys, eps, eps_phys, eta, Re_lambda, Te, urms, lambda, l0;
+  double cfl, umax, kmax_eta, kmax_eta_sqrt2;
+  double skew[3], flat[3];
+  double phi_var, phi_prod, phi_prod_phys, chi, chi_phys;
+  double skew_phi[3], flat_phi[3];
+  double A, E_forced, P_inj;
+  int64_t step;
+} psc_stats;
+
+typedef struct psc_sim psc_sim;
+
+/* Bytes of device workspace needed for these parameters.  Fails with
+ * PSC_EUNSUPPORTED_N for an unsupported N and PSC_EINVAL for bad parameters. */
+psc_status psc_workspace_size(const psc_params* p, size_t* bytes);
+
+/* Grid sizes this build supports (ascending); returns how many, writes at most cap. */
+int32_t psc_supported_sizes(int32_t* out, int32_t cap);
+
+/* Create a simulation on the current CUDA device.  dev_ws: caller-owned device
+ * memory of ws_bytes >= psc_workspace_size() bytes, 256-byte aligned, kept alive
+ * until psc_destroy().  stream: a cudaStream_t (NULL = default stream).
+ * The state is zero until psc_init_field() or psc_set_state(). */
+psc_status psc_create(const psc_params* p, void* dev_ws, size_t ws_bytes, void* stream,
+                      psc_sim** out);
+
+/* Initial condition (section 2.3): the random solenoidal field with the chosen
+ * shell spectrum, or the Taylor-Green vortex plus that noise; phi = 0.
+ * Deterministic in (seed, N, ic).  Resets t and the step counter.  Synchronises. */
+psc_status psc_init_field(psc_sim* s);
+
+/* Advance nsteps RK4 steps (section 2.2), asynchronously on the stream. */
+psc_status psc_step(psc_sim* s, int32_t nsteps);
+
+/* Statistics of the current state.  Ek and Ephi (host, may be NULL) receive up
+ * to nshell_cap shell values E(n), E_phi(n), n = floor(|k|+1/2); *nshell (may
+ * be NULL) receives the number of shells.  out (host, may be NULL) receives the
+ * record.  Synchronises; returns PSC_EUNSTABLE if a non-finite velocity was seen. */
+psc_status psc_spectra_and_stats(psc_sim* s, double* Ek, double* Ephi, int32_t nshell_cap,
+                                 int32_t* nshell, psc_stats* out);
+
+/* Bytes of the compact state (4 fields). */
+psc_status psc_state_bytes(const psc_sim* s, size_t* bytes);
+
+/* Copy the compact state to / from host or device memory (any pointer CUDA can
+ * address).  set_state also accepts an initial state from the caller.  Both
+ * synchronise the stream. */
+psc_status psc_get_state(psc_sim* s, void* dst, size_t bytes);
+psc_status psc_set_state(psc_sim* s, const void* src, size_t bytes);
+
+/* One evaluation of the right-hand side without the linear terms,
+ * N(u, phi) = (P(u x omega)_k + A u_k 1_F, -(u.grad phi)_k - beta u2_k),
+ * for a compact state at device pointer `in`, written in compact layout to the
+ * device pointer `out` (both psc_state_bytes() long, not overlapping the
+ * workspace).  With the plain RK4 integrator the linear terms are included.
+ * Asynchronous on the stream. */
+psc_status psc_rhs(psc_sim* s, const void* in, void* out);
+
+/* Time, step counter and current dt (host values; synchronises). */
+psc_status psc_time(psc_sim* s, double* t, int64_t* step, double* dt);
+
+/* Kernel classes for profiling. */
+typedef enum {
+  PSC_K_FORCING = 0,  /* band energy and forcing amplitude                   */
+  PSC_K_ZINV = 1,     /* inverse transform along z (+ d/dz streams)          */
+  PSC_K_YINV = 2,     /* inverse transform along y (+ omega_x, d/dy streams) */
+  PSC_K_XPASS = 3,    /* fused x transforms and nonlinear products           */
+  PSC_K_YFWD = 4,     /* forward transform along y, truncation               */
+  PSC_K_ZFWD = 5,     /* forward transform along z, truncation               */
+  PSC_K_COMBINE = 6,  /* projection, forcing, scalar source, RK stage update */
+  PSC_K_OTHER = 7,    /* CFL, IF tables, statistics passes and reductions, IC */
+  PSC_K_NKIND = 8
+} psc_kernel_kind;
+
+/* Profiling: while enabled, every kernel launch of this simulation is
+ * bracketed by CUDA events on its stream.  psc_profile_read() synchronises,
+ * writes the summed device milliseconds and launch counts per kernel kind
+ * (arrays of nkind <= PSC_K_NKIND entries, either may be NULL) and clears them. */
+psc_status psc_profile_enable(psc_sim* s, int32_t on);
+psc_status psc_profile_read(psc_sim* s, double* ms, int64_t* launches, int32_t nkind);
+
+/* Total kernels this simulation has launched since creation (always counted). */
+psc_status psc_launch_count(const psc_sim* s, int64_t* n);
+
+psc_status psc_destroy(psc_sim* s);
+
+/* Message for the last failing call on this thread (never NULL). */
+const char* psc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSC_H */

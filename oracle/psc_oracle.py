@@ -573,3 +573,74 @@ def run(p: Params, nsteps: int, uh=None, ph=None, with_records: bool = True):
     if with_records:
         recs.append(dict(step=nsteps, **stats(uh, ph, g, p, t, dt)))
     return uh, ph, recs, t, dt
+
+
+# --------------------------------------------------------------------------
+# Direct triad sums for sparse states (any N)
+# --------------------------------------------------------------------------
+
+def rhs_sparse_triads(modes, N: int, p: Params):
+    """N(u, phi) of a state with few non-zero modes, by direct summation.
+
+    ``modes`` maps (kx, ky, kz) with kx >= 0 and |k_i| <= K to
+    (u1, u2, u3, phi) unnormalised coefficients; kx = 0 entries must come in
+    conjugate pairs.  With u(x) = N^-3 sum_p u_p exp(i p.x) (Eq. 5), the
+    products of the retained modes are alias-free on the retained set, so
+
+        (u x omega)_k   = N^-3 sum_{p+q=k} u_p x (i q x u_q)
+        (u.grad phi)_k  = N^-3 sum_{p+q=k} (u_p . i q) phi_q
+
+    over the full (conjugate-completed) mode set.  Returns a dict over the
+    output modes k (kx >= 0, |k_i| <= K) that receive a contribution or carry
+    forcing/source terms: k -> (r1, r2, r3, r_phi) as in rhs_nonlinear."""
+    K = (N - 1) // 3
+    full = {}
+    for (kx, ky, kz), v in modes.items():
+        v = np.asarray(v, dtype=np.complex128)
+        full[(kx, ky, kz)] = v
+        if kx > 0:
+            full[(-kx, -ky, -kz)] = np.conj(v)
+    keys = list(full)
+    kv = np.array(keys, dtype=np.int64)
+    vals = np.array([full[k] for k in keys])
+    # forcing amplitude from the band energy of the stored half
+    A = 0.0
+    if p.forcing == FORCE_CONST_POWER:
+        s = 0.0
+        for (kx, ky, kz), v in modes.items():
+            k2 = kx * kx + ky * ky + kz * kz
+            if 0 < k2 <= p.kF * p.kF:
+                s += (1.0 if kx == 0 else 2.0) * float(np.sum(np.abs(v[:3]) ** 2))
+        ef = s / (2.0 * float(N) ** 6)
+        A = p.eps_inj / (2.0 * ef) if ef > 1e-300 else 0.0
+    acc_u, acc_s = {}, {}
+    for a in range(len(keys)):
+        pvec = kv[a]
+        up = vals[a][:3]
+        for b in range(len(keys)):
+            q = kv[b]
+            k = pvec + q
+            if k[0] < 0 or np.any(np.abs(k) > K):
+                continue
+            uq, phq = vals[b][:3], vals[b][3]
+            om = 1j * np.cross(q.astype(np.float64), uq)
+            kk = tuple(int(c) for c in k)
+            acc_u[kk] = acc_u.get(kk, 0) + np.cross(up, om)
+            acc_s[kk] = acc_s.get(kk, 0) + np.dot(up, 1j * q.astype(np.float64)) * phq
+    out = {}
+    n3 = float(N) ** 3
+    for kk in set(acc_u) | set(modes):
+        k = np.array(kk, dtype=np.float64)
+        k2 = float(k @ k)
+        nl = np.asarray(acc_u.get(kk, np.zeros(3, dtype=complex)), dtype=np.complex128) / n3
+        if k2 > 0:
+            nl = nl - k * (k @ nl) / k2
+        else:
+            nl = np.zeros(3, dtype=np.complex128)
+        v = np.asarray(modes.get(kk, np.zeros(4, dtype=complex)), dtype=np.complex128)
+        if 0 < k2 <= p.kF * p.kF:
+            nl = nl + A * v[:3]
+        sh = complex(acc_s.get(kk, 0.0)) / n3
+        rp = (-sh - p.beta * v[1]) if p.scalar_on else 0.0
+        out[kk] = np.array([nl[0], nl[1], nl[2], rp], dtype=np.complex128)
+    return out

@@ -1,0 +1,621 @@
+// Host side of the C ABI (include/psc.h): parameter checks, workspace
+// layout, stage orchestration and assembly of the statistics record.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "psc.h"
+#include "psc_kernels.cuh"
+
+// ---------------------------------------------------------------- dispatch
+
+// Grid sizes with compiled pass kernels (one object file per size and precision).
+#define PSC_SIZES(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(512) X(1024)
+#define PSC_DECL(n)                                  \
+  const psc::PassTable* psc_pass_table_float_##n();  \
+  const psc::PassTable* psc_pass_table_double_##n();
+PSC_SIZES(PSC_DECL)
+#undef PSC_DECL
+
+namespace psc {
+
+const PassTable* table_f32(int N) {
+  switch (N) {
+#define PSC_CASE(n) case n: return psc_pass_table_float_##n();
+    PSC_SIZES(PSC_CASE)
+#undef PSC_CASE
+    default: return nullptr;
+  }
+}
+const PassTable* table_f64(int N) {
+  switch (N) {
+#define PSC_CASE(n) case n: return psc_pass_table_double_##n();
+    PSC_SIZES(PSC_CASE)
+#undef PSC_CASE
+    default: return nullptr;
+  }
+}
+
+static const int kSizes[] = {
+#define PSC_LIST(n) n,
+    PSC_SIZES(PSC_LIST)
+#undef PSC_LIST
+};
+
+static bool size_supported(int N) {
+  for (int n : kSizes)
+    if (n == N) return true;
+  return false;
+}
+
+// ---------------------------------------------------------------- errors
+
+static thread_local std::string g_err;
+
+static psc_status fail(psc_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+static psc_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(PSC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define PSC_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+#define PSC_LAUNCHED(where)                             \
+  do {                                                  \
+    cudaError_t e_ = cudaGetLastError();                \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+// ---------------------------------------------------------------- layout
+
+static int num_shells(int N) {
+  const int K = (N - 1) / 3;
+  return (int)std::floor(std::sqrt(3.0 * K * K) + 0.5) + 1;
+}
+
+struct Layout {
+  size_t ctrl, U, V, Acc, zreg, yreg, tw, eu, ep, partials, shells, fac, total;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static Layout make_layout(const Dims& d, int fp64, int xwarps) {
+  const size_t cs = fp64 ? 16 : 8, rs = fp64 ? 8 : 4;
+  const size_t S = (size_t)d.S, zs = (size_t)d.zs, ys = (size_t)d.ys;
+  size_t zreg = Z_NSTREAM * zs;
+  if (4 * ys > zreg) zreg = 4 * ys;
+  if (4 * S > zreg) zreg = 4 * S;
+  size_t yreg = Y_NSTREAM * ys * cs;
+  if (4 * zs * cs > yreg) yreg = 4 * zs * cs;
+  if (3 * S * 16 > yreg) yreg = 3 * S * 16;  // FP64 scratch of the initial condition
+  const int nsh = num_shells(d.N);
+  Layout L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
+  L.ctrl = take(sizeof(Ctrl));
+  L.U = take(4 * S * cs);
+  L.V = take(4 * S * cs);
+  L.Acc = take(4 * S * cs);
+  L.zreg = take(zreg * cs);
+  L.yreg = take(yreg);
+  L.tw = take(d.N * cs);
+  L.eu = take((d.K + 1) * rs);
+  L.ep = take((d.K + 1) * rs);
+  L.partials = take((size_t)xwarps * NQ * 8);
+  L.shells = take((size_t)NSQ * nsh * 8);
+  L.fac = take((size_t)nsh * 8);
+  L.total = o;
+  return L;
+}
+
+// exp(-2 pi i j / N) to FP64 accuracy: reduce to a quarter turn exactly, then
+// rotate by whole quarter turns.
+static void twiddle(long j, long N, double* c, double* s) {
+  j %= N;
+  const long q = (4 * j) / N;
+  const long rem = 4 * j - q * N;  // angle = q pi/2 + (pi/2) rem/N
+  const double th = (M_PI / 2.0) * ((double)rem / (double)N);
+  double c0 = std::cos(th), s0 = std::sin(th);
+  for (long r = 0; r < q; ++r) {  // multiply by i
+    const double t = c0;
+    c0 = -s0;
+    s0 = t;
+  }
+  *c = c0;
+  *s = -s0;  // forward sign
+}
+
+}  // namespace psc
+
+using namespace psc;
+
+struct psc_sim {
+  psc_params p;
+  Dims d;
+  int fp64;
+  const PassTable* tb;
+  cudaStream_t st;
+  unsigned char* ws;
+  Layout L;
+  Ctrl* ctrl;
+  int64_t step;
+  int nshell;
+  // launch accounting and optional per-launch event timing
+  int64_t launches = 0;
+  bool profiling = false;
+  struct Timed { int kind; cudaEvent_t a, b; };
+  std::vector<Timed> timed;
+  std::vector<cudaEvent_t> pool;
+};
+
+namespace {
+
+cudaEvent_t take_event(psc_sim* s) {
+  if (!s->pool.empty()) {
+    cudaEvent_t e = s->pool.back();
+    s->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Run `launch` (which enqueues kernels on s->st) as `n` launches of `kind`.
+template <class F> void launch(psc_sim* s, int kind, int n, F&& f) {
+  s->launches += n;
+  if (!s->profiling) {
+    f();
+    return;
+  }
+  psc_sim::Timed t{kind, take_event(s), take_event(s)};
+  cudaEventRecord(t.a, s->st);
+  f();
+  cudaEventRecord(t.b, s->st);
+  s->timed.push_back(t);
+}
+
+}  // namespace
+
+static psc_status check_params(const psc_params* p) {
+  if (!p) return fail(PSC_EINVAL, "null params");
+  if (!size_supported(p->N)) return fail(PSC_EUNSUPPORTED_N, "unsupported grid size N=" + std::to_string(p->N));
+  if (p->precision != PSC_FP64 && p->precision != PSC_FP32_MIXED) return fail(PSC_EINVAL, "bad precision");
+  if (!(p->nu >= 0.0) || !(p->Sc > 0.0)) return fail(PSC_EINVAL, "nu must be >= 0 and Sc > 0");
+  if (p->cfl <= 0.0 && !(p->dt > 0.0)) return fail(PSC_EINVAL, "dt must be > 0 when cfl <= 0");
+  if (p->record_every < 1) return fail(PSC_EINVAL, "record_every must be >= 1");
+  if (p->forcing != PSC_FORCE_NONE && p->forcing != PSC_FORCE_CONST_POWER) return fail(PSC_EINVAL, "bad forcing");
+  if (p->integrator != PSC_INTEG_IFRK4 && p->integrator != PSC_INTEG_RK4) return fail(PSC_EINVAL, "bad integrator");
+  if (p->ic < 0 || p->ic > 2) return fail(PSC_EINVAL, "bad ic");
+  if (!(p->kF >= 0.0) || !(p->eps_inj >= 0.0)) return fail(PSC_EINVAL, "kF and eps_inj must be >= 0");
+  if (!(p->ic_energy >= 0.0) || !(p->ic_noise_frac >= 0.0)) return fail(PSC_EINVAL, "IC energies must be >= 0");
+  return PSC_OK;
+}
+
+static const PassTable* pick_table(const psc_params* p) {
+  return p->precision == PSC_FP64 ? table_f64(p->N) : table_f32(p->N);
+}
+
+extern "C" {
+
+const char* psc_last_error(void) { return g_err.c_str(); }
+
+int32_t psc_supported_sizes(int32_t* out, int32_t cap) {
+  const int n = (int)(sizeof(kSizes) / sizeof(kSizes[0]));
+  for (int i = 0; i < n && i < cap; ++i) out[i] = kSizes[i];
+  return n;
+}
+
+psc_status psc_workspace_size(const psc_params* p, size_t* bytes) {
+  psc_status s = check_params(p);
+  if (s != PSC_OK) return s;
+  if (!bytes) return fail(PSC_EINVAL, "null bytes");
+  const PassTable* tb = pick_table(p);
+  *bytes = make_layout(make_dims(p->N), p->precision == PSC_FP64, tb->xwarps).total;
+  return PSC_OK;
+}
+
+psc_status psc_create(const psc_params* p, void* dev_ws, size_t ws_bytes, void* stream, psc_sim** out) {
+  psc_status s = check_params(p);
+  if (s != PSC_OK) return s;
+  if (!out || !dev_ws) return fail(PSC_EINVAL, "null workspace or output handle");
+  if (((uintptr_t)dev_ws & 255) != 0) return fail(PSC_EINVAL, "workspace must be 256-byte aligned");
+  const PassTable* tb = pick_table(p);
+  Layout L = make_layout(make_dims(p->N), p->precision == PSC_FP64, tb->xwarps);
+  if (ws_bytes < L.total)
+    return fail(PSC_ENOMEM_BUDGET, "workspace of " + std::to_string(ws_bytes) + " bytes < required " +
+                                       std::to_string(L.total));
+  psc_sim* sim = new (std::nothrow) psc_sim();
+  if (!sim) return fail(PSC_EINVAL, "host allocation failed");
+  sim->p = *p;
+  sim->d = make_dims(p->N);
+  sim->fp64 = p->precision == PSC_FP64;
+  sim->tb = tb;
+  sim->st = (cudaStream_t)stream;
+  sim->ws = (unsigned char*)dev_ws;
+  sim->L = L;
+  sim->ctrl = (Ctrl*)(sim->ws + L.ctrl);
+  sim->step = 0;
+  sim->nshell = num_shells(p->N);
+  // twiddles, control block, zero state
+  const int N = p->N;
+  std::vector<double> twd(2 * (size_t)N);
+  for (int j = 0; j < N; ++j) twiddle(j, N, &twd[2 * j], &twd[2 * j + 1]);
+  std::vector<float> twf(2 * (size_t)N);
+  for (size_t i = 0; i < twd.size(); ++i) twf[i] = (float)twd[i];
+  Ctrl c0;
+  std::memset(&c0, 0, sizeof(c0));
+  c0.dt = p->dt;
+  cudaError_t e;
+  if (sim->fp64) e = cudaMemcpyAsync(sim->ws + L.tw, twd.data(), twd.size() * 8, cudaMemcpyHostToDevice, sim->st);
+  else e = cudaMemcpyAsync(sim->ws + L.tw, twf.data(), twf.size() * 4, cudaMemcpyHostToDevice, sim->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sim->ctrl, &c0, sizeof(c0), cudaMemcpyHostToDevice, sim->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sim->ws + L.U, 0, L.V - L.U, sim->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(sim->st);
+  if (e != cudaSuccess) {
+    delete sim;
+    return cuda_fail(e, "psc_create");
+  }
+  *out = sim;
+  return PSC_OK;
+}
+
+psc_status psc_destroy(psc_sim* s) {
+  if (!s) return PSC_OK;
+  for (auto& t : s->timed) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  for (auto e : s->pool) cudaEventDestroy(e);
+  delete s;
+  return PSC_OK;
+}
+
+psc_status psc_profile_enable(psc_sim* s, int32_t on) {
+  if (!s) return fail(PSC_EINVAL, "null sim");
+  s->profiling = on != 0;
+  return PSC_OK;
+}
+
+psc_status psc_profile_read(psc_sim* s, double* ms, int64_t* launches, int32_t nkind) {
+  if (!s) return fail(PSC_EINVAL, "null sim");
+  if (nkind < 0 || nkind > PSC_K_NKIND) return fail(PSC_EINVAL, "bad nkind");
+  PSC_CUDA(cudaStreamSynchronize(s->st));
+  std::vector<double> t(PSC_K_NKIND, 0.0);
+  std::vector<int64_t> n(PSC_K_NKIND, 0);
+  for (auto& e : s->timed) {
+    float x = 0.f;
+    PSC_CUDA(cudaEventElapsedTime(&x, e.a, e.b));
+    t[e.kind] += x;
+    n[e.kind] += 1;
+    s->pool.push_back(e.a);
+    s->pool.push_back(e.b);
+  }
+  s->timed.clear();
+  for (int k = 0; k < nkind; ++k) {
+    if (ms) ms[k] = t[k];
+    if (launches) launches[k] = n[k];
+  }
+  return PSC_OK;
+}
+
+psc_status psc_launch_count(const psc_sim* s, int64_t* n) {
+  if (!s || !n) return fail(PSC_EINVAL, "null argument");
+  *n = s->launches;
+  return PSC_OK;
+}
+
+psc_status psc_state_bytes(const psc_sim* s, size_t* bytes) {
+  if (!s || !bytes) return fail(PSC_EINVAL, "null argument");
+  *bytes = 4 * (size_t)s->d.S * (s->fp64 ? 16 : 8);
+  return PSC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- internals
+
+namespace {
+
+PassArgs pass_args(psc_sim* s, const void* in) {
+  PassArgs a;
+  a.d = s->d;
+  a.in = in;
+  a.zb = s->ws + s->L.zreg;
+  a.yb = s->ws + s->L.yreg;
+  a.xb = s->ws + s->L.zreg;  // the z-inverse streams are dead once the y-inverse pass has run
+  a.yf = s->ws + s->L.yreg;  // the y-inverse streams are dead once the X pass has run
+  a.rb = s->ws + s->L.zreg;  // the X-pass output is dead once the y-forward pass has run
+  a.tw = s->ws + s->L.tw;
+  a.partials = (double*)(s->ws + s->L.partials);
+  a.ctrl = s->ctrl;
+  a.want_umax = 0;
+  a.st = s->st;
+  return a;
+}
+
+template <typename T>
+void launch_famp(psc_sim* s, const void* in) {
+  launch(s, PSC_K_FORCING, 1, [&] {
+    k_famp<T><<<1, 32, 0, s->st>>>(s->d, in, s->ctrl, s->p.kF * s->p.kF, s->p.eps_inj, s->p.forcing);
+  });
+}
+
+template <typename T>
+void launch_iftab(psc_sim* s) {
+  const int n = s->d.K + 1;
+  launch(s, PSC_K_OTHER, 1, [&] {
+    k_iftab<T><<<(n + 127) / 128, 128, 0, s->st>>>(s->d.K, s->ctrl, s->p.nu, s->p.nu / s->p.Sc,
+                                                     (T*)(s->ws + s->L.eu), (T*)(s->ws + s->L.ep));
+  });
+}
+
+CombineArgs combine_args(psc_sim* s, const void* vin) {
+  CombineArgs c;
+  c.d = s->d;
+  c.rb = s->ws + s->L.zreg;
+  c.vin = vin;
+  c.U = s->ws + s->L.U;
+  c.V = s->ws + s->L.V;
+  c.Acc = s->ws + s->L.Acc;
+  c.out = nullptr;
+  c.eu = s->ws + s->L.eu;
+  c.ep = s->ws + s->L.ep;
+  c.ctrl = s->ctrl;
+  c.kF2 = s->p.kF * s->p.kF;
+  c.beta = s->p.beta;
+  c.nu = s->p.nu;
+  c.D = s->p.nu / s->p.Sc;
+  c.forcing = s->p.forcing;
+  c.integrator = s->p.integrator;
+  c.scalar_on = s->p.scalar_on;
+  return c;
+}
+
+template <typename T>
+void launch_combine(psc_sim* s, int stage, const CombineArgs& c) {
+  const long long S = s->d.S;
+  const int blocks = (int)((S + 255) / 256);
+  launch(s, PSC_K_COMBINE, 1, [&] {
+    switch (stage) {
+      case 0: k_combine<T, 0><<<blocks, 256, 0, s->st>>>(c); break;
+      case 1: k_combine<T, 1><<<blocks, 256, 0, s->st>>>(c); break;
+      case 2: k_combine<T, 2><<<blocks, 256, 0, s->st>>>(c); break;
+      case 3: k_combine<T, 3><<<blocks, 256, 0, s->st>>>(c); break;
+      default: k_combine<T, 4><<<blocks, 256, 0, s->st>>>(c); break;
+    }
+  });
+}
+
+// The five FFT passes of one RHS evaluation of `in`, leaving the unprojected
+// compact (NL, u.grad phi) in the z region.
+template <typename T>
+void rhs_passes(psc_sim* s, const void* in, bool umax) {
+  PassArgs a = pass_args(s, in);
+  a.want_umax = umax ? 1 : 0;
+  if (umax) cudaMemsetAsync(&s->ctrl->umax_bits, 0, sizeof(unsigned long long), s->st);
+  launch_famp<T>(s, in);
+  launch(s, PSC_K_ZINV, 1, [&] { s->tb->zinv(a, false); });
+  launch(s, PSC_K_YINV, 1, [&] { s->tb->yinv(a, false); });
+  launch(s, PSC_K_XPASS, 1, [&] { s->tb->xpass(a, XMODE_RHS); });
+  if (umax && s->p.cfl > 0.0) {
+    launch(s, PSC_K_OTHER, 1, [&] { k_cfl<<<1, 32, 0, s->st>>>(s->ctrl, s->p.cfl, 2.0 * M_PI / s->p.N); });
+    launch_iftab<T>(s);
+  }
+  launch(s, PSC_K_YFWD, 1, [&] { s->tb->yfwd(a); });
+  launch(s, PSC_K_ZFWD, 1, [&] { s->tb->zfwd(a); });
+}
+
+template <typename T>
+psc_status do_step(psc_sim* s, int nsteps) {
+  unsigned char* U = s->ws + s->L.U;
+  unsigned char* V = s->ws + s->L.V;
+  for (int n = 0; n < nsteps; ++n) {
+    const bool reset_dt = s->p.cfl > 0.0 && (s->step % s->p.record_every) == 0;
+    for (int stage = 1; stage <= 4; ++stage) {
+      const void* vin = stage == 1 ? (const void*)U : (const void*)V;
+      rhs_passes<T>(s, vin, stage == 1 && reset_dt);
+      launch_combine<T>(s, stage, combine_args(s, vin));
+    }
+    PSC_LAUNCHED("psc_step");
+    ++s->step;
+  }
+  return PSC_OK;
+}
+
+template <typename T>
+psc_status do_rhs(psc_sim* s, const void* in, void* out) {
+  rhs_passes<T>(s, in, false);
+  CombineArgs c = combine_args(s, in);
+  c.out = out;
+  launch_combine<T>(s, 0, c);
+  PSC_LAUNCHED("psc_rhs");
+  return PSC_OK;
+}
+
+template <typename T>
+psc_status do_init(psc_sim* s) {
+  const Dims& d = s->d;
+  double2* z = (double2*)(s->ws + s->L.yreg);
+  double* shells = (double*)(s->ws + s->L.shells);
+  double* fac = (double*)(s->ws + s->L.fac);
+  const int blocks = (int)((d.S + 255) / 256);
+  const bool tg = s->p.ic == PSC_IC_TAYLOR_GREEN_NOISE;
+  const double K0 = tg ? s->p.ic_noise_frac * 0.125 : s->p.ic_energy;
+  const int shape = s->p.ic == PSC_IC_PAPER_EQ9 ? 2 : 0;
+  const double n3 = (double)d.N * d.N * d.N;
+  launch(s, PSC_K_OTHER, 4, [&] {
+    k_ic_draw<<<blocks, 256, 0, s->st>>>(d, (unsigned long long)s->p.seed, z);
+    k_shells<double><<<s->nshell, 256, 0, s->st>>>(d, z, nullptr, s->nshell, shells);
+    k_ic_factors<<<1, 32, 0, s->st>>>(s->nshell, shells, 1.0 / (2.0 * n3 * n3), K0, shape, s->p.kF, fac);
+    k_ic_finish<T><<<blocks, 256, 0, s->st>>>(d, z, fac, tg ? 1 : 0, s->ws + s->L.U);
+  });
+  Ctrl c0;
+  std::memset(&c0, 0, sizeof(c0));
+  c0.dt = s->p.dt;
+  PSC_CUDA(cudaMemcpyAsync(s->ctrl, &c0, sizeof(c0), cudaMemcpyHostToDevice, s->st));
+  launch_iftab<T>(s);
+  PSC_LAUNCHED("psc_init_field");
+  PSC_CUDA(cudaStreamSynchronize(s->st));
+  s->step = 0;
+  return PSC_OK;
+}
+
+template <typename T>
+psc_status do_stats(psc_sim* s, double* Ek, double* Ephi, int cap, int* nshell, psc_stats* out) {
+  const Dims& d = s->d;
+  const void* U = s->ws + s->L.U;
+  PassArgs a = pass_args(s, U);
+  PSC_CUDA(cudaMemsetAsync(&s->ctrl->umax_bits, 0, sizeof(unsigned long long), s->st));
+  launch_famp<T>(s, U);
+  launch(s, PSC_K_OTHER, 3, [&] {
+    s->tb->zinv(a, true);
+    s->tb->yinv(a, true);
+    s->tb->xpass(a, XMODE_STATS);
+  });
+  double* shells = (double*)(s->ws + s->L.shells);
+  launch(s, PSC_K_OTHER, 2, [&] {
+    k_reduce_moments<<<1, 32, 0, s->st>>>(a.partials, s->tb->xwarps, s->ctrl);
+    k_shells<T><<<s->nshell, 256, 0, s->st>>>(d, U, (const unsigned char*)U + 3 * d.S * (s->fp64 ? 16 : 8),
+                                               s->nshell, shells);
+  });
+  PSC_LAUNCHED("psc_spectra_and_stats");
+  Ctrl c;
+  std::vector<double> sh((size_t)NSQ * s->nshell);
+  PSC_CUDA(cudaMemcpyAsync(&c, s->ctrl, sizeof(c), cudaMemcpyDeviceToHost, s->st));
+  PSC_CUDA(cudaMemcpyAsync(sh.data(), shells, sh.size() * 8, cudaMemcpyDeviceToHost, s->st));
+  PSC_CUDA(cudaStreamSynchronize(s->st));
+  if (c.err & 1) return fail(PSC_ECUDA, "device index check failed");
+  const int ns = s->nshell;
+  const double n3 = (double)d.N * d.N * d.N, n6 = n3 * n3;
+  const double nu = s->p.nu, D = s->p.nu / s->p.Sc, beta = s->p.beta;
+  double Ks = 0, dK = 0, Vp = 0, dV = 0, pr = 0;
+  for (int n = 0; n < ns; ++n) {
+    const double E = sh[0 * ns + n] / (2 * n6), Ep = sh[1 * ns + n] / (2 * n6);
+    if (Ek && n < cap) Ek[n] = E;
+    if (Ephi && n < cap) Ephi[n] = Ep;
+    Ks += E;
+    Vp += Ep;
+    dK += sh[2 * ns + n] / (2 * n6);
+    dV += sh[3 * ns + n] / (2 * n6);
+    pr += sh[4 * ns + n] / n6;
+  }
+  if (nshell) *nshell = ns;
+  double umax;
+  std::memcpy(&umax, &c.umax_bits, sizeof(umax));
+  if (out) {
+    psc_stats& r = *out;
+    std::memset(&r, 0, sizeof(r));
+    const double* m = c.moments;
+    r.t = c.t;
+    r.dt = c.dt;
+    // at a CFL reset step the record carries the dt that step will use (Eq. 10)
+    if (s->p.cfl > 0.0 && (s->step % s->p.record_every) == 0 && umax > 0.0 &&
+        umax <= 1.7976931348623157e308)
+      r.dt = s->p.cfl * (2.0 * M_PI / d.N) / umax;
+    r.step = s->step;
+    r.K = Ks;
+    r.K_phys = 0.5 * m[0] / n3;
+    r.eps = 2.0 * nu * dK;
+    r.eps_phys = nu * m[1] / n3;
+    r.urms = std::sqrt(2.0 * Ks / 3.0);
+    const double eps = r.eps;
+    r.eta = eps > 0 ? std::pow(nu * nu * nu / eps, 0.25) : INFINITY;
+    r.lambda = eps > 0 ? r.urms * std::sqrt(15.0 * nu / eps) : INFINITY;
+    r.Re_lambda = eps > 0 && nu > 0 ? r.lambda * r.urms / nu : INFINITY;
+    r.l0 = eps > 0 ? r.urms * r.urms * r.urms / eps : INFINITY;
+    r.Te = r.urms > 0 ? r.l0 / r.urms : INFINITY;
+    r.umax = umax;
+    r.cfl = r.dt / (2.0 * M_PI / d.N) * umax;
+    r.kmax_eta = (d.N / 3.0) * r.eta;
+    r.kmax_eta_sqrt2 = (std::sqrt(2.0) * d.N / 3.0) * r.eta;
+    for (int i = 0; i < 3; ++i) {
+      const double m2 = m[2 + 3 * i] / n3, m3 = m[3 + 3 * i] / n3, m4 = m[4 + 3 * i] / n3;
+      r.skew[i] = m2 > 0 ? m3 / std::pow(m2, 1.5) : 0.0;
+      r.flat[i] = m2 > 0 ? m4 / (m2 * m2) : 0.0;
+      const double p2 = m[11 + 3 * i] / n3, p3 = m[12 + 3 * i] / n3, p4 = m[13 + 3 * i] / n3;
+      r.skew_phi[i] = p2 > 0 ? p3 / std::pow(p2, 1.5) : 0.0;
+      r.flat_phi[i] = p2 > 0 ? p4 / (p2 * p2) : 0.0;
+    }
+    r.phi_var = m[21] / n3;
+    r.phi_prod = -2.0 * beta * pr;
+    r.phi_prod_phys = -2.0 * beta * m[20] / n3;
+    r.chi = 2.0 * D * 2.0 * dV;
+    r.chi_phys = 2.0 * D * (m[11] + m[14] + m[17]) / n3;
+    r.A = c.A;
+    r.E_forced = c.Ef;
+    r.P_inj = 2.0 * c.A * c.Ef;
+  }
+  (void)Vp;
+  if ((c.err & 2) || !(umax <= 1.7976931348623157e308))
+    return fail(PSC_EUNSTABLE, "non-finite velocity in the CFL monitor");
+  return PSC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+psc_status psc_init_field(psc_sim* s) {
+  if (!s) return fail(PSC_EINVAL, "null sim");
+  return s->fp64 ? do_init<double>(s) : do_init<float>(s);
+}
+
+psc_status psc_step(psc_sim* s, int32_t nsteps) {
+  if (!s) return fail(PSC_EINVAL, "null sim");
+  if (nsteps < 0) return fail(PSC_EINVAL, "nsteps must be >= 0");
+  return s->fp64 ? do_step<double>(s, nsteps) : do_step<float>(s, nsteps);
+}
+
+psc_status psc_rhs(psc_sim* s, const void* in, void* out) {
+  if (!s || !in || !out) return fail(PSC_EINVAL, "null argument");
+  return s->fp64 ? do_rhs<double>(s, in, out) : do_rhs<float>(s, in, out);
+}
+
+psc_status psc_spectra_and_stats(psc_sim* s, double* Ek, double* Ephi, int32_t cap, int32_t* nshell,
+                                 psc_stats* out) {
+  if (!s) return fail(PSC_EINVAL, "null sim");
+  if (cap < 0) return fail(PSC_EINVAL, "negative capacity");
+  return s->fp64 ? do_stats<double>(s, Ek, Ephi, cap, nshell, out)
+                 : do_stats<float>(s, Ek, Ephi, cap, nshell, out);
+}
+
+psc_status psc_get_state(psc_sim* s, void* dst, size_t bytes) {
+  size_t nb;
+  if (!s || !dst) return fail(PSC_EINVAL, "null argument");
+  psc_state_bytes(s, &nb);
+  if (bytes != nb) return fail(PSC_EINVAL, "state size mismatch");
+  PSC_CUDA(cudaMemcpyAsync(dst, s->ws + s->L.U, nb, cudaMemcpyDefault, s->st));
+  PSC_CUDA(cudaStreamSynchronize(s->st));
+  return PSC_OK;
+}
+
+psc_status psc_set_state(psc_sim* s, const void* src, size_t bytes) {
+  size_t nb;
+  if (!s || !src) return fail(PSC_EINVAL, "null argument");
+  psc_state_bytes(s, &nb);
+  if (bytes != nb) return fail(PSC_EINVAL, "state size mismatch");
+  PSC_CUDA(cudaMemcpyAsync(s->ws + s->L.U, src, nb, cudaMemcpyDefault, s->st));
+  PSC_CUDA(cudaStreamSynchronize(s->st));
+  return PSC_OK;
+}
+
+psc_status psc_time(psc_sim* s, double* t, int64_t* step, double* dt) {
+  if (!s) return fail(PSC_EINVAL, "null sim");
+  Ctrl c;
+  PSC_CUDA(cudaMemcpyAsync(&c, s->ctrl, sizeof(c), cudaMemcpyDeviceToHost, s->st));
+  PSC_CUDA(cudaStreamSynchronize(s->st));
+  if (t) *t = c.t;
+  if (dt) *dt = c.dt;
+  if (step) *step = s->step;
+  return PSC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Internal declarations shared by the host API and the per-(precision, N)
+// kernel instantiations.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace psc {
+
+// Number of FP64 physical-space moments the statistics pass accumulates.
+//  0 sum u.u            1 sum |omega|^2
+//  2..4  (du1/dx1)^2,3,4   5..7 (du2/dx2)^2,3,4   8..10 (du3/dx3)^2,3,4
+// 11..13 (dphi/dx1)^2,3,4 14..16 (dphi/dx2)^2,3,4 17..19 (dphi/dx3)^2,3,4
+// 20 sum phi u2        21 sum phi^2
+constexpr int NQ = 24;
+
+// Per-shell quantities of the spectral statistics: E, E_phi, sum k^2 E,
+// sum k^2 E_phi, sum w Re(conj(phi) u2)/N^6.
+constexpr int NSQ = 5;
+
+struct Dims {
+  int N, K, M, P;
+  long long S;   // compact elements per field: P*P*M
+  long long zs;  // one stream of the z-transformed stage: N*P*M
+  long long ys;  // one stream of the y-transformed stage: N*N*M
+};
+
+inline Dims make_dims(int N) {
+  Dims d;
+  d.N = N;
+  d.K = (N - 1) / 3;
+  d.M = d.K + 1;
+  d.P = 2 * d.K + 1;
+  d.S = (long long)d.P * d.P * d.M;
+  d.zs = (long long)N * d.P * d.M;
+  d.ys = (long long)N * N * d.M;
+  return d;
+}
+
+// Device-resident control block: scalars every pass reads or writes.
+struct Ctrl {
+  double t, dt;
+  double A, Ef;                   // forcing amplitude, band energy of the last forced state
+  unsigned long long umax_bits;   // max |u1|+|u2|+|u3| as the bits of a non-negative double
+  int err;                        // bit 0: index check failed; bit 1: non-finite velocity
+  int pad;
+  double moments[NQ];
+};
+
+// Streams of the intermediate buffers (indices into zb / yb).
+enum { Z_UX, Z_UY, Z_UZ, Z_DZUY, Z_DZUX, Z_PHI, Z_DZPHI, Z_DZUZ, Z_NSTREAM };
+enum { Y_UX, Y_UY, Y_UZ, Y_WX, Y_DZUX, Y_DYUX, Y_PHI, Y_DYPHI, Y_DZPHI, Y_DYUY, Y_DZUZ, Y_NSTREAM };
+
+struct PassArgs {
+  Dims d;
+  const void* in;   // stage input, compact 4 fields
+  void* zb;         // z-inverse output  [Z_NSTREAM][N][P][M]
+  void* yb;         // y-inverse output  [Y_NSTREAM][N][N][M]
+  void* xb;         // x-pass output     [4][N][N][M]   (aliases zb)
+  void* yf;         // y-forward output  [4][N][P][M]   (aliases yb)
+  void* rb;         // z-forward output  [4][P][P][M]   compact, unprojected
+  const void* tw;   // exp(-2 pi i j/N), j < N
+  double* partials; // X-pass statistics partials [xwarps][NQ]
+  Ctrl* ctrl;
+  int want_umax;    // X pass also reduces max |u1|+|u2|+|u3|
+  cudaStream_t st;
+};
+
+enum { XMODE_RHS = 0, XMODE_STATS = 1 };
+
+struct PassTable {
+  void (*zinv)(const PassArgs&, bool stats);
+  void (*yinv)(const PassArgs&, bool stats);
+  void (*xpass)(const PassArgs&, int mode);
+  void (*yfwd)(const PassArgs&);
+  void (*zfwd)(const PassArgs&);
+  int xwarps;       // warps launched by the X pass (rows of `partials`)
+};
+
+const PassTable* table_f32(int N);
+const PassTable* table_f64(int N);
+
+}  // namespace psc

@@ -1,0 +1,701 @@
+// The five FFT passes of one right-hand-side evaluation (section 2.2 and 2.3
+// of arXiv:2012.04838: u_hat and i k u_hat are transformed back, the
+// nonlinear terms are formed in physical space and transformed forward):
+//
+//   Z-inverse : compact state -> lines along kz zero-padded to N, inverse DFT;
+//               also emits d/dz streams (i kz multiplied before the transform)
+//   Y-inverse : lines along ky zero-padded to N, inverse DFT; forms
+//               omega_x = d_y u_z - d_z u_y, d_y u_x and d_y phi from i ky
+//   X (fused) : per (z, y) row, 9 complex-to-real transforms (packed two per
+//               complex DFT), u x omega and u . grad phi, 4 real-to-complex
+//               transforms packed in pairs, keep kx <= K.  Physical fields never
+//               leave the chip.  The statistics variant accumulates FP64
+//               moments of the velocity/scalar gradients instead (Eqs. 11-13).
+//   Y-forward : lines along y, forward DFT, keep |ky| <= K
+//   Z-forward : lines along z, forward DFT, keep |kz| <= K -> compact RHS
+//
+// All transforms are the unnormalised DFTs of Eq. 5; the 1/N^3 of the
+// inverse is applied once, to the physical fields in the X pass.
+#pragma once
+
+#include "psc_common.cuh"
+
+namespace psc {
+
+// ---------------------------------------------------------------------------
+// Strided passes: a CTA transforms W adjacent kx columns of one plane; the
+// line runs along the strided (outer) axis, so every line element moved is a
+// W-wide contiguous run of complex values.
+// ---------------------------------------------------------------------------
+
+template <typename T, int N> struct StridedCfg {
+  static constexpr int W = (sizeof(T) == 4) ? ((N >= 512) ? 8 : 16) : 8;
+  static constexpr int THREADS = W * PlanD<N>::TPL;
+  // cap registers at 128 per thread so at least 512 threads fit on an SM
+  static constexpr int MINB = THREADS >= 512 ? 1 : 512 / THREADS;
+};
+
+template <typename T, int N, int W> struct StridedSmem {
+  using C = typename CT<T>::type;
+  static constexpr int R1 = PlanD<N>::R1, R2 = PlanD<N>::R2;
+  // rows of R2*W values; rows start W*sizeof(C) bytes apart modulo 128 so the
+  // column-major reads of step 2 spread over all banks
+  static constexpr int CPB = 128 / (int)sizeof(C);
+  static constexpr int PAD = (W >= CPB) ? 0 : ((((W - R2 * W) % CPB) + CPB) % CPB);
+  static constexpr int ROW = R2 * W + PAD;
+  static constexpr size_t BYTES = (size_t)R1 * ROW * sizeof(C);
+};
+
+// One length-N DFT per column, direction DIR (-1 forward, +1 inverse).
+// ld(p) returns the element at line position p; st(k, v) stores output k.
+template <typename T, int N, int W, int DIR, class LD, class ST>
+__device__ __forceinline__ void strided_fft(const LD& ld, const ST& st,
+                                            typename CT<T>::type* sm,
+                                            const typename CT<T>::type* __restrict__ tw,
+                                            int t, int w) {
+  using C = typename CT<T>::type;
+  using PL = PlanD<N>;
+  using SM = StridedSmem<T, N, W>;
+  constexpr int R1 = PL::R1, R2 = PL::R2, TPL = PL::TPL, J1 = PL::J1, J2 = PL::J2;
+#pragma unroll
+  for (int j = 0; j < J1; ++j) {
+    const int n2 = t + j * TPL;
+    C a[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) a[n1] = ld(R2 * n1 + n2);
+    Dft<R1, DIR>::template run<T, C>(a);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      C v = a[k1];
+      if (k1 > 0) {
+        const C wv = tw[n2 * k1];
+        v = (DIR < 0) ? cmul(v, wv) : cmulc(v, wv);
+      }
+      sm[k1 * SM::ROW + n2 * W + w] = v;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < J2; ++j) {
+    const int k1 = t + j * TPL;
+    C b[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) b[n2] = sm[k1 * SM::ROW + n2 * W + w];
+    Dft<R2, DIR>::template run<T, C>(b);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) st(k1 + R1 * k2, b[k2]);
+  }
+  __syncthreads();
+}
+
+// wavenumber of line position p of a zero-padded / truncated axis; false if
+// the position is outside |k| <= K
+template <int N> __device__ __forceinline__ bool k_of_pos(int p, int& k) {
+  constexpr int K = (N - 1) / 3;
+  if (p <= K) { k = p; return true; }
+  if (p >= N - K) { k = p - N; return true; }
+  return false;
+}
+
+template <typename T, int N, bool STATS>
+__global__ void __launch_bounds__(StridedCfg<T, N>::THREADS, StridedCfg<T, N>::MINB)
+k_zinv(PassArgs a) {
+  using C = typename CT<T>::type;
+  constexpr int W = StridedCfg<T, N>::W, K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int w = threadIdx.x, t = threadIdx.y;
+  const int ix = blockIdx.x * W + w;
+  const int iy = blockIdx.y;
+  const bool act = ix < M;
+  const C* __restrict__ in = static_cast<const C*>(a.in);
+  C* __restrict__ zb = static_cast<C*>(a.zb);
+  const C* __restrict__ tw = static_cast<const C*>(a.tw);
+  const long long S = (long long)P * P * M, zs = (long long)N * P * M;
+  const C zero = mk(T(0), T(0));
+
+  auto load = [&](int f, int p, bool deriv) -> C {
+    int kz;
+    if (!act || !k_of_pos<N>(p, kz)) return zero;
+    const long long idx = f * S + ((long long)(kz + K) * P + iy) * M + ix;
+    if (!PSC_OK_INDEX(idx, 4 * S, a.ctrl)) return zero;
+    const C v = in[idx];
+    return deriv ? mul_ik(v, T(kz)) : v;
+  };
+  auto run = [&](int f, bool deriv, int s) {
+    strided_fft<T, N, W, +1>(
+        [&](int p) { return load(f, p, deriv); },
+        [&](int z, C v) {
+          if (!act) return;
+          const long long idx = s * zs + ((long long)z * P + iy) * M + ix;
+          if (PSC_OK_INDEX(idx, (long long)Z_NSTREAM * zs, a.ctrl)) zb[idx] = v;
+        },
+        sm, tw, t, w);
+  };
+  run(0, false, Z_UX);
+  run(1, false, Z_UY);
+  run(2, false, Z_UZ);
+  run(1, true, Z_DZUY);
+  run(0, true, Z_DZUX);
+  run(3, false, Z_PHI);
+  run(3, true, Z_DZPHI);
+  if (STATS) run(2, true, Z_DZUZ);
+}
+
+template <typename T, int N, bool STATS>
+__global__ void __launch_bounds__(StridedCfg<T, N>::THREADS, StridedCfg<T, N>::MINB)
+k_yinv(PassArgs a) {
+  using C = typename CT<T>::type;
+  constexpr int W = StridedCfg<T, N>::W, K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int w = threadIdx.x, t = threadIdx.y;
+  const int ix = blockIdx.x * W + w;
+  const int z = blockIdx.y;
+  const bool act = ix < M;
+  const C* __restrict__ zb = static_cast<const C*>(a.zb);
+  C* __restrict__ yb = static_cast<C*>(a.yb);
+  const C* __restrict__ tw = static_cast<const C*>(a.tw);
+  const long long zs = (long long)N * P * M, ys = (long long)N * N * M;
+  const C zero = mk(T(0), T(0));
+
+  auto zl = [&](int s, int ky) -> C {
+    const long long idx = s * zs + ((long long)z * P + (ky + K)) * M + ix;
+    if (!PSC_OK_INDEX(idx, (long long)Z_NSTREAM * zs, a.ctrl)) return zero;
+    return zb[idx];
+  };
+  // kind 0: stream s1; 1: i ky s1; 2: i ky s1 - s2
+  auto run = [&](int kind, int s1, int s2, int so) {
+    strided_fft<T, N, W, +1>(
+        [&](int p) -> C {
+          int ky;
+          if (!act || !k_of_pos<N>(p, ky)) return zero;
+          if (kind == 0) return zl(s1, ky);
+          const C d = mul_ik(zl(s1, ky), T(ky));
+          return kind == 1 ? d : csub(d, zl(s2, ky));
+        },
+        [&](int y, C v) {
+          if (!act) return;
+          const long long idx = so * ys + ((long long)z * N + y) * M + ix;
+          if (PSC_OK_INDEX(idx, (long long)Y_NSTREAM * ys, a.ctrl)) yb[idx] = v;
+        },
+        sm, tw, t, w);
+  };
+  run(0, Z_UX, 0, Y_UX);
+  run(0, Z_UY, 0, Y_UY);
+  run(0, Z_UZ, 0, Y_UZ);
+  run(2, Z_UZ, Z_DZUY, Y_WX);      // omega_x = d_y u_z - d_z u_y
+  run(0, Z_DZUX, 0, Y_DZUX);
+  run(1, Z_UX, 0, Y_DYUX);
+  run(0, Z_PHI, 0, Y_PHI);
+  run(1, Z_PHI, 0, Y_DYPHI);
+  run(0, Z_DZPHI, 0, Y_DZPHI);
+  if (STATS) {
+    run(1, Z_UY, 0, Y_DYUY);
+    run(0, Z_DZUZ, 0, Y_DZUZ);
+  }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(StridedCfg<T, N>::THREADS, StridedCfg<T, N>::MINB)
+k_yfwd(PassArgs a) {
+  using C = typename CT<T>::type;
+  constexpr int W = StridedCfg<T, N>::W, K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int w = threadIdx.x, t = threadIdx.y;
+  const int ix = blockIdx.x * W + w;
+  const int z = blockIdx.y;
+  const bool act = ix < M;
+  const C* __restrict__ xb = static_cast<const C*>(a.xb);
+  C* __restrict__ yf = static_cast<C*>(a.yf);
+  const C* __restrict__ tw = static_cast<const C*>(a.tw);
+  const long long zs = (long long)N * P * M, ys = (long long)N * N * M;
+  const C zero = mk(T(0), T(0));
+#pragma unroll 1
+  for (int s = 0; s < 4; ++s) {
+    strided_fft<T, N, W, -1>(
+        [&](int y) -> C {
+          if (!act) return zero;
+          const long long idx = s * ys + ((long long)z * N + y) * M + ix;
+          if (!PSC_OK_INDEX(idx, 4 * ys, a.ctrl)) return zero;
+          return xb[idx];
+        },
+        [&](int k, C v) {
+          int ky;
+          if (!act || !k_of_pos<N>(k, ky)) return;
+          const long long idx = s * zs + ((long long)z * P + (ky + K)) * M + ix;
+          if (PSC_OK_INDEX(idx, 4 * zs, a.ctrl)) yf[idx] = v;
+        },
+        sm, tw, t, w);
+  }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(StridedCfg<T, N>::THREADS, StridedCfg<T, N>::MINB)
+k_zfwd(PassArgs a) {
+  using C = typename CT<T>::type;
+  constexpr int W = StridedCfg<T, N>::W, K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int w = threadIdx.x, t = threadIdx.y;
+  const int ix = blockIdx.x * W + w;
+  const int iy = blockIdx.y;
+  const bool act = ix < M;
+  const C* __restrict__ yf = static_cast<const C*>(a.yf);
+  C* __restrict__ rb = static_cast<C*>(a.rb);
+  const C* __restrict__ tw = static_cast<const C*>(a.tw);
+  const long long S = (long long)P * P * M, zs = (long long)N * P * M;
+  const C zero = mk(T(0), T(0));
+#pragma unroll 1
+  for (int s = 0; s < 4; ++s) {
+    strided_fft<T, N, W, -1>(
+        [&](int z) -> C {
+          if (!act) return zero;
+          const long long idx = s * zs + ((long long)z * P + iy) * M + ix;
+          if (!PSC_OK_INDEX(idx, 4 * zs, a.ctrl)) return zero;
+          return yf[idx];
+        },
+        [&](int k, C v) {
+          int kz;
+          if (!act || !k_of_pos<N>(k, kz)) return;
+          const long long idx = s * S + ((long long)(kz + K) * P + iy) * M + ix;
+          if (PSC_OK_INDEX(idx, 4 * S, a.ctrl)) rb[idx] = v;
+        },
+        sm, tw, t, w);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// X pass: one warp transforms 32/TPL adjacent rows (z, y); TPL lanes per row.
+// ---------------------------------------------------------------------------
+
+template <typename T, int N> struct XCfg {
+  using C = typename CT<T>::type;
+  using PL = PlanD<N>;
+  static constexpr int TPL = PL::TPL, LPW = 32 / TPL;
+  static constexpr int WARPS = 4;
+  static constexpr int PER = N / TPL;         // values per thread per field
+  static constexpr bool STASH = PER >= 20;    // velocity parked in shared memory
+  static constexpr int ROWI = PL::R2 + 1;     // inverse exchange rows (odd stride)
+  static constexpr int ROWF = PL::R1 + 1;     // forward exchange rows
+  static constexpr int EX0 = PL::R1 * ROWI > PL::R2 * ROWF ? PL::R1 * ROWI : PL::R2 * ROWF;
+  static constexpr int EXCH = EX0 > N ? EX0 : N;
+  static constexpr int STASH_REALS = STASH ? 3 * N : 0;
+  static constexpr size_t LINE_BYTES =
+      ((EXCH * sizeof(C) + STASH_REALS * sizeof(T)) + 15) / 16 * 16;
+  static constexpr size_t SMEM = LINE_BYTES * LPW * WARPS;
+};
+
+// Inverse DFT of one row from its half spectrum, two real fields at once:
+// Z[p] = X1[p] + i X2[p] (p <= K; imaginary parts dropped at p = 0),
+// conj(X1[N-p]) + i conj(X2[N-p]) (p >= N-K), 0 elsewhere.  On return
+// z[j][k2] holds scale * IDFT(Z) at position (t + j TPL) + R1 k2, whose real
+// and imaginary parts are the two real fields.
+template <typename T, int N, class SPEC>
+__device__ __forceinline__ void xinv(const SPEC& spec,
+                                     typename CT<T>::type (&z)[PlanD<N>::J2][PlanD<N>::R2],
+                                     typename CT<T>::type* ex,
+                                     const typename CT<T>::type* __restrict__ tw, int t, T scale) {
+  using C = typename CT<T>::type;
+  using PL = PlanD<N>;
+  using XC = XCfg<T, N>;
+  constexpr int R1 = PL::R1, R2 = PL::R2, TPL = PL::TPL, K = PL::K;
+#pragma unroll
+  for (int j = 0; j < PL::J1; ++j) {
+    const int n2 = t + j * TPL;
+    C a[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) {
+      const int p = R2 * n1 + n2;
+      C x1, x2;
+      if (p <= K) {
+        spec(p, x1, x2);
+        if (p == 0) { x1.y = T(0); x2.y = T(0); }
+        a[n1] = mk(x1.x - x2.y, x1.y + x2.x);
+      } else if (p >= N - K) {
+        spec(N - p, x1, x2);
+        a[n1] = mk(x1.x + x2.y, x2.x - x1.y);
+      } else {
+        a[n1] = mk(T(0), T(0));
+      }
+    }
+    Dft<R1, +1>::template run<T, C>(a);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      C v = a[k1];
+      if (k1 > 0) v = cmulc(v, tw[n2 * k1]);
+      ex[k1 * XC::ROWI + n2] = v;
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < PL::J2; ++j) {
+    const int k1 = t + j * TPL;
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) z[j][n2] = ex[k1 * XC::ROWI + n2];
+    Dft<R2, +1>::template run<T, C>(z[j]);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) z[j][k2] = cscale(z[j][k2], scale);
+  }
+  __syncwarp();
+}
+
+// Forward DFT of a row holding two real fields packed as x1 + i x2 at the
+// positions xinv leaves them in; out(kx, X1, X2) receives both half spectra
+// for kx <= K: X1 = (Z[k] + conj Z[N-k])/2, X2 = (Z[k] - conj Z[N-k])/(2i).
+template <typename T, int N, class OUT>
+__device__ __forceinline__ void xfwd(typename CT<T>::type (&x)[PlanD<N>::J2][PlanD<N>::R2],
+                                     const OUT& out, typename CT<T>::type* ex,
+                                     const typename CT<T>::type* __restrict__ tw, int t) {
+  using C = typename CT<T>::type;
+  using PL = PlanD<N>;
+  using XC = XCfg<T, N>;
+  constexpr int R1 = PL::R1, R2 = PL::R2, TPL = PL::TPL, K = PL::K;
+  // transposed plan: n = R1 n1' + n2' with n2' = t + j TPL < R1, n1' < R2
+#pragma unroll
+  for (int j = 0; j < PL::J2; ++j) {
+    const int n2 = t + j * TPL;
+    Dft<R2, -1>::template run<T, C>(x[j]);
+#pragma unroll
+    for (int k1 = 0; k1 < R2; ++k1) {
+      C v = x[j][k1];
+      if (k1 > 0) v = cmul(v, tw[n2 * k1]);
+      ex[k1 * XC::ROWF + n2] = v;
+    }
+  }
+  __syncwarp();
+  C b[PL::J1][R1];
+#pragma unroll
+  for (int j = 0; j < PL::J1; ++j) {
+    const int k1 = t + j * TPL;
+#pragma unroll
+    for (int n2 = 0; n2 < R1; ++n2) b[j][n2] = ex[k1 * XC::ROWF + n2];
+    Dft<R1, -1>::template run<T, C>(b[j]);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < PL::J1; ++j) {
+    const int k1 = t + j * TPL;
+#pragma unroll
+    for (int k2 = 0; k2 < R1; ++k2) ex[k1 + R2 * k2] = b[j][k2];
+  }
+  __syncwarp();
+  for (int kx = t; kx <= K; kx += TPL) {
+    const C A = ex[kx];
+    const C B = ex[kx == 0 ? 0 : N - kx];
+    out(kx, mk(T(0.5) * (A.x + B.x), T(0.5) * (A.y - B.y)),
+        mk(T(0.5) * (A.y + B.y), T(0.5) * (B.x - A.x)));
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void umax_update(Ctrl* c, double v) {
+  atomicMax(&c->umax_bits, (unsigned long long)__double_as_longlong(v));
+}
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(32 * XCfg<T, N>::WARPS)
+k_xpass(PassArgs a) {
+  using C = typename CT<T>::type;
+  using PL = PlanD<N>;
+  using XC = XCfg<T, N>;
+  constexpr int R1 = PL::R1, R2 = PL::R2, TPL = PL::TPL, J2 = PL::J2, M = PL::M;
+  constexpr int LPW = XC::LPW;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int t = lane % TPL, g = lane / TPL;
+  unsigned char* myline = smraw + (size_t)(wid * LPW + g) * XC::LINE_BYTES;
+  C* ex = reinterpret_cast<C*>(myline);
+  T* stash = reinterpret_cast<T*>(myline + XC::EXCH * sizeof(C));
+  const C* __restrict__ yb = static_cast<const C*>(a.yb);
+  C* __restrict__ xb = static_cast<C*>(a.xb);
+  const C* __restrict__ tw = static_cast<const C*>(a.tw);
+  const long long ys = (long long)N * N * M;
+  const long long nlines = (long long)N * N;
+  const T scale = T(1.0 / ((double)N * N * N));
+  const C zero = mk(T(0), T(0));
+  double umax = 0.0;
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+
+#pragma unroll 1
+  for (long long grp = (long long)blockIdx.x * XC::WARPS + wid; grp * LPW < nlines;
+       grp += (long long)gridDim.x * XC::WARPS) {
+    const long long line = grp * LPW + g;
+    const bool valid = line < nlines;
+    auto Y = [&](int s, int kx) -> C {
+      if (!valid) return zero;
+      const long long idx = s * ys + line * M + kx;
+      if (!PSC_OK_INDEX(idx, (long long)Y_NSTREAM * ys, a.ctrl)) return zero;
+      return yb[idx];
+    };
+    auto pos = [&](int j, int k2) { return (t + j * TPL) + R1 * k2; };
+    C z[J2][R2];
+
+    if constexpr (MODE == XMODE_RHS) {
+      T ux[J2][R2], uy[J2][R2], uz[J2][R2];
+      T nlx[J2][R2], nly[J2][R2], nlz[J2][R2], sv[J2][R2];
+      auto getu = [&](int c, int j, int k2) -> T {
+        if constexpr (XC::STASH) return stash[c * N + pos(j, k2)];
+        else return c == 0 ? ux[j][k2] : (c == 1 ? uy[j][k2] : uz[j][k2]);
+      };
+      // (u1, u2)
+      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UY, kx); }, z, ex, tw, t, scale);
+#pragma unroll
+      for (int j = 0; j < J2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) {
+          if constexpr (XC::STASH) {
+            stash[0 * N + pos(j, k2)] = z[j][k2].x;
+            stash[1 * N + pos(j, k2)] = z[j][k2].y;
+          } else {
+            ux[j][k2] = z[j][k2].x;
+            uy[j][k2] = z[j][k2].y;
+          }
+        }
+      // (u3, omega_1)
+      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UZ, kx); x2 = Y(Y_WX, kx); }, z, ex, tw, t, scale);
+#pragma unroll
+      for (int j = 0; j < J2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) {
+          const T u3 = z[j][k2].x, w1 = z[j][k2].y;
+          if constexpr (XC::STASH) stash[2 * N + pos(j, k2)] = u3;
+          else uz[j][k2] = u3;
+          nly[j][k2] = u3 * w1;
+          nlz[j][k2] = -getu(1, j, k2) * w1;
+          if (a.want_umax) {
+            const double s3 = (double)(fabs(getu(0, j, k2)) + fabs(getu(1, j, k2)) + fabs(u3));
+            umax = s3 > umax || s3 != s3 ? s3 : umax;
+          }
+        }
+      // (omega_2, omega_3):  omega_2 = d_z u_1 - i kx u_3,  omega_3 = i kx u_2 - d_y u_1
+      xinv<T, N>(
+          [&](int kx, C& x1, C& x2) {
+            x1 = csub(Y(Y_DZUX, kx), mul_ik(Y(Y_UZ, kx), T(kx)));
+            x2 = csub(mul_ik(Y(Y_UY, kx), T(kx)), Y(Y_DYUX, kx));
+          },
+          z, ex, tw, t, scale);
+#pragma unroll
+      for (int j = 0; j < J2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) {
+          const T w2 = z[j][k2].x, w3 = z[j][k2].y;
+          const T u1 = getu(0, j, k2), u2 = getu(1, j, k2), u3 = getu(2, j, k2);
+          nlx[j][k2] = u2 * w3 - u3 * w2;
+          nly[j][k2] -= u1 * w3;
+          nlz[j][k2] += u1 * w2;
+        }
+      // forward (NL1, NL2)
+#pragma unroll
+      for (int j = 0; j < J2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) z[j][k2] = mk(nlx[j][k2], nly[j][k2]);
+      xfwd<T, N>(z,
+                 [&](int kx, C X1, C X2) {
+                   if (!valid) return;
+                   const long long i0 = line * M + kx;
+                   if (PSC_OK_INDEX(i0 + ys, 4 * ys, a.ctrl)) {
+                     xb[i0] = X1;
+                     xb[ys + i0] = X2;
+                   }
+                 },
+                 ex, tw, t);
+      // (dphi/dx1, dphi/dx2)
+      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_PHI, kx), T(kx)); x2 = Y(Y_DYPHI, kx); },
+                 z, ex, tw, t, scale);
+#pragma unroll
+      for (int j = 0; j < J2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2)
+          sv[j][k2] = getu(0, j, k2) * z[j][k2].x + getu(1, j, k2) * z[j][k2].y;
+      // (dphi/dx3, 0)
+      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZPHI, kx); x2 = zero; }, z, ex, tw, t, scale);
+#pragma unroll
+      for (int j = 0; j < J2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) {
+          sv[j][k2] += getu(2, j, k2) * z[j][k2].x;
+          z[j][k2] = mk(nlz[j][k2], sv[j][k2]);
+        }
+      // forward (NL3, u.grad phi)
+      xfwd<T, N>(z,
+                 [&](int kx, C X1, C X2) {
+                   if (!valid) return;
+                   const long long i0 = line * M + kx;
+                   if (PSC_OK_INDEX(i0 + 3 * ys, 4 * ys, a.ctrl)) {
+                     xb[2 * ys + i0] = X1;
+                     xb[3 * ys + i0] = X2;
+                   }
+                 },
+                 ex, tw, t);
+    } else {
+      // statistics: moments of the diagonal velocity gradients and the scalar
+      // gradient (Eqs. 11-12), |omega|^2, u.u, phi u2, phi^2 (Eq. 13)
+      T s13[J2][R2];
+      auto mom = [&](int q, T v) { (void)q; return v; };
+      (void)mom;
+      auto acc234 = [&](int q, int j, int k2, T v) {
+        const T v2 = v * v;
+        acc[q] += (double)v2;
+        acc[q + 1] += (double)(v2 * v);
+        acc[q + 2] += (double)(v2 * v2);
+        (void)j; (void)k2;
+      };
+      // (u1, u3)
+      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UZ, kx); }, z, ex, tw, t, scale);
+#pragma unroll
+      for (int j = 0; j < J2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) {
+          const T u1 = z[j][k2].x, u3 = z[j][k2].y;
+          acc[0] += (double)(u1 * u1 + u3 * u3);
+          s13[j][k2] = fabs(u1) + fabs(u3);
+        }
+      // (u2, phi)
+      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UY, kx); x2 = Y(Y_PHI, kx); }, z, ex, tw, t, scale);
+#pragma unroll
+      for (int j = 0; j < J2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) {
+          const T u2 = z[j][k2].x, ph = z[j][k2].y;
+          acc[0] += (double)(u2 * u2);
+          acc[20] += (double)(ph * u2);
+          acc[21] += (double)(ph * ph);
+          const double s3 = (double)(s13[j][k2] + fabs(u2));
+          umax = s3 > umax || s3 != s3 ? s3 : umax;
+        }
+      // (omega_1, omega_2)
+      xinv<T, N>(
+          [&](int kx, C& x1, C& x2) {
+            x1 = Y(Y_WX, kx);
+            x2 = csub(Y(Y_DZUX, kx), mul_ik(Y(Y_UZ, kx), T(kx)));
+          },
+          z, ex, tw, t, scale);
+#pragma unroll
+      for (int j = 0; j < J2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2)
+          acc[1] += (double)(z[j][k2].x * z[j][k2].x + z[j][k2].y * z[j][k2].y);
+      // (omega_3, dphi/dx1)
+      xinv<T, N>(
+          [&](int kx, C& x1, C& x2) {
+            x1 = csub(mul_ik(Y(Y_UY, kx), T(kx)), Y(Y_DYUX, kx));
+            x2 = mul_ik(Y(Y_PHI, kx), T(kx));
+          },
+          z, ex, tw, t, scale);
+#pragma unroll
+      for (int j = 0; j < J2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) {
+          acc[1] += (double)(z[j][k2].x * z[j][k2].x);
+          acc234(11, j, k2, z[j][k2].y);
+        }
+      // (dphi/dx2, dphi/dx3)
+      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DYPHI, kx); x2 = Y(Y_DZPHI, kx); }, z, ex, tw, t,
+                 scale);
+#pragma unroll
+      for (int j = 0; j < J2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) {
+          acc234(14, j, k2, z[j][k2].x);
+          acc234(17, j, k2, z[j][k2].y);
+        }
+      // (du1/dx1, du2/dx2)
+      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_UX, kx), T(kx)); x2 = Y(Y_DYUY, kx); }, z,
+                 ex, tw, t, scale);
+#pragma unroll
+      for (int j = 0; j < J2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) {
+          acc234(2, j, k2, z[j][k2].x);
+          acc234(5, j, k2, z[j][k2].y);
+        }
+      // (du3/dx3, 0)
+      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZUZ, kx); x2 = zero; }, z, ex, tw, t, scale);
+#pragma unroll
+      for (int j = 0; j < J2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) acc234(8, j, k2, z[j][k2].x);
+    }
+  }
+
+  if (MODE == XMODE_STATS || a.want_umax) {
+    for (int o = 16; o > 0; o >>= 1) {
+      const double other = __shfl_xor_sync(0xffffffffu, umax, o);
+      umax = other > umax || other != other ? other : umax;
+    }
+    if (lane == 0) umax_update(a.ctrl, umax);
+  }
+  if constexpr (MODE == XMODE_STATS) {
+    const long long gw = (long long)blockIdx.x * XC::WARPS + wid;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double v = acc[q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) a.partials[gw * NQ + q] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+
+template <typename T, int N> struct Passes {
+  static constexpr int W = StridedCfg<T, N>::W;
+  static constexpr int TPL = PlanD<N>::TPL;
+  static constexpr int M = PlanD<N>::M, P = PlanD<N>::P;
+  static constexpr size_t SSM = StridedSmem<T, N, W>::BYTES;
+
+  static int xgrid() {
+    const long long groups = ((long long)N * N + XCfg<T, N>::LPW - 1) / XCfg<T, N>::LPW;
+    long long g = (groups + XCfg<T, N>::WARPS - 1) / XCfg<T, N>::WARPS;
+    const long long cap = 152 * 8;
+    return (int)(g < cap ? g : cap);
+  }
+
+  template <class KER> static void prep(KER k, size_t smem) {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+
+  static void zinv(const PassArgs& a, bool stats) {
+    dim3 grid((M + W - 1) / W, P), block(W, TPL);
+    if (stats) { prep(k_zinv<T, N, true>, SSM); k_zinv<T, N, true><<<grid, block, SSM, a.st>>>(a); }
+    else { prep(k_zinv<T, N, false>, SSM); k_zinv<T, N, false><<<grid, block, SSM, a.st>>>(a); }
+  }
+  static void yinv(const PassArgs& a, bool stats) {
+    dim3 grid((M + W - 1) / W, N), block(W, TPL);
+    if (stats) { prep(k_yinv<T, N, true>, SSM); k_yinv<T, N, true><<<grid, block, SSM, a.st>>>(a); }
+    else { prep(k_yinv<T, N, false>, SSM); k_yinv<T, N, false><<<grid, block, SSM, a.st>>>(a); }
+  }
+  static void xpass(const PassArgs& a, int mode) {
+    const size_t sm = XCfg<T, N>::SMEM;
+    dim3 block(32 * XCfg<T, N>::WARPS);
+    if (mode == XMODE_STATS) {
+      prep(k_xpass<T, N, XMODE_STATS>, sm);
+      k_xpass<T, N, XMODE_STATS><<<xgrid(), block, sm, a.st>>>(a);
+    } else {
+      prep(k_xpass<T, N, XMODE_RHS>, sm);
+      k_xpass<T, N, XMODE_RHS><<<xgrid(), block, sm, a.st>>>(a);
+    }
+  }
+  static void yfwd(const PassArgs& a) {
+    dim3 grid((M + W - 1) / W, N), block(W, TPL);
+    prep(k_yfwd<T, N>, SSM);
+    k_yfwd<T, N><<<grid, block, SSM, a.st>>>(a);
+  }
+  static void zfwd(const PassArgs& a) {
+    dim3 grid((M + W - 1) / W, P), block(W, TPL);
+    prep(k_zfwd<T, N>, SSM);
+    k_zfwd<T, N><<<grid, block, SSM, a.st>>>(a);
+  }
+  static const PassTable* table() {
+    static const PassTable tb = {&zinv, &yinv, &xpass, &yfwd, &zfwd, xgrid() * XCfg<T, N>::WARPS};
+    return &tb;
+  }
+};
+
+}  // namespace psc

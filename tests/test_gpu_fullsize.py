@@ -1,0 +1,132 @@
+"""Full-size checks at 1024^3 FP32-mixed, in the launch configuration the
+benchmark times.  The oracle cannot transform a 1024^3 field, so the checks use
+(a) a sparse state whose right-hand side the oracle sums triad by triad, and
+(b) properties of the initial condition that hold at any size."""
+import numpy as np
+import pytest
+
+from oracle import psc_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+B = pytest.importorskip("paper_2012_04838_gb300.binding")
+
+N = 1024
+K = (N - 1) // 3
+
+
+@pytest.fixture(scope="module")
+def sim():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    free, _ = torch.cuda.mem_get_info()
+    p = B.Params(N=N, precision=B.FP32_MIXED, nu=3.341e-4, Sc=1.0, beta=1.0, eps_inj=0.1, kF=2.0,
+                 cfl=0.5, ic=B.IC_SPECTRUM_K4, seed=3, ic_energy=1.5, record_every=10)
+    if free < B.workspace_size(p) + 16e9:
+        pytest.skip("not enough device memory for the 1024^3 case")
+    s = B.Simulation(p, device="cuda:0")
+    yield s
+    s.close()
+
+
+def _sparse_modes(seed):
+    rng = np.random.default_rng(seed)
+    ks = [(1, 0, 1), (0, 2, -1), (2, 1, 0), (1, -1, 2), (3, 2, -2), (5, -4, 1), (K, -K, 7),
+          (K - 3, K, -K), (200, -150, 90), (0, 1, 1), (120, K, 0), (2, 0, 0)]
+    modes = {}
+    for k in ks:
+        v = (rng.standard_normal(4) + 1j * rng.standard_normal(4)) * float(N) ** 3 * 0.05
+        modes[k] = v
+        if k[0] == 0:
+            modes[(0, -k[1], -k[2])] = np.conj(v)
+    return modes
+
+
+def test_fullsize_rhs_on_sparse_state_matches_triad_sums(sim):
+    modes = _sparse_modes(1)
+    dev = torch.device("cuda:0")
+    x = torch.zeros(B.compact_shape(N), dtype=torch.complex64, device=dev)
+    rounded = {}
+    for (kx, ky, kz), v in modes.items():
+        v32 = v.astype(np.complex64)
+        rounded[(kx, ky, kz)] = v32.astype(np.complex128)
+        x[:, kz + K, ky + K, kx] = torch.from_numpy(v32).to(dev)
+    out = sim.rhs(x)
+    ref = O.rhs_sparse_triads(rounded, N, O.Params(N=N, nu=sim.p.nu, Sc=sim.p.Sc, beta=sim.p.beta,
+                                                   eps_inj=sim.p.eps_inj, kF=sim.p.kF))
+    scale = max(np.abs(v).max() for v in ref.values())
+    mask = torch.zeros(B.compact_shape(N)[1:], dtype=torch.bool, device=dev)
+    got, want = [], []
+    for (kx, ky, kz), v in ref.items():
+        got.append(out[:, kz + K, ky + K, kx].cpu().numpy().astype(np.complex128))
+        want.append(v)
+        mask[kz + K, ky + K, kx] = True
+    got, want = np.array(got), np.array(want)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 2e-6
+    assert np.abs(got - want).max() < 2e-6 * scale
+    # everything else is round-off
+    rest = out.abs().amax(dim=0)
+    rest[mask] = 0
+    assert float(rest.max()) < 2e-6 * scale
+
+
+def test_fullsize_initial_condition_properties(sim):
+    sim.init_field()
+    rec, E, Ep = sim.stats()
+    assert abs(rec["K"] - 1.5) < 1e-6 * 1.5
+    assert abs(E.sum() - rec["K"]) < 1e-9
+    assert abs(rec["K_phys"] - rec["K"]) < 1e-5 * rec["K"]
+    assert abs(rec["eps_phys"] - rec["eps"]) < 1e-5 * rec["eps"]
+    tgt = O.target_shell_energy(len(E), O.IC_SPECTRUM_K4, 1.0, 2.0)
+    tgt = tgt * 1.5 / tgt.sum()
+    big = tgt > 1e-8 * tgt.max()
+    assert np.allclose(E[big], tgt[big], rtol=1e-5)
+    assert np.abs(Ep).max() == 0.0
+    # Gaussian velocity-gradient statistics of the random-phase IC (section 3.1)
+    for i in range(3):
+        assert abs(rec["skew"][i]) < 0.02 and abs(rec["flat"][i] - 3.0) < 0.05
+    st = sim.get_state()
+    dev = st.device
+    kx = torch.arange(0, K + 1, device=dev, dtype=torch.float32).view(1, 1, -1)
+    ky = torch.arange(-K, K + 1, device=dev, dtype=torch.float32).view(1, -1, 1)
+    kz = ky.view(-1, 1, 1)
+    div = kx * st[0] + ky * st[1] + kz * st[2]
+    mag = torch.sqrt(kx * kx + ky * ky + kz * kz) * (st[0].abs() + st[1].abs() + st[2].abs())
+    assert float(div.abs().max()) <= 1e-5 * float(mag.max())
+    # sampled modes: same direction as the oracle's raw draw, a positive factor apart
+    for k in [(1, 2, 3), (0, 4, -1), (7, -3, 2), (17, 0, -9)]:
+        raw = _oracle_raw_draw(3, *k)
+        g = st[:3, k[2] + K, k[1] + K, k[0]].cpu().numpy().astype(np.complex128)
+        r = g / raw
+        assert np.allclose(r.imag, 0, atol=1e-5 * abs(r[0])) and r.real.min() > 0
+        assert np.allclose(r.real, r.real[0], rtol=1e-5)
+    del st
+
+
+def _oracle_raw_draw(seed, kx, ky, kz):
+    """The oracle's projected raw draw of one canonical mode (its IC recipe)."""
+    key = np.array([O.mode_key(kx, ky, kz)], dtype=np.uint64)
+    z = []
+    for c in range(3):
+        u1 = O.uniform01(seed, key * np.uint64(8) + np.uint64(2 * c))
+        u2 = O.uniform01(seed, key * np.uint64(8) + np.uint64(2 * c + 1))
+        r = np.sqrt(-2.0 * np.log(u1))
+        z.append((r * np.cos(2 * np.pi * u2) + 1j * r * np.sin(2 * np.pi * u2))[0])
+    z = np.array(z)
+    k = np.array([kx, ky, kz], dtype=np.float64)
+    return z - k * (k @ z) / (k @ k)
+
+
+def test_fullsize_steps_conserve_budget(sim):
+    # two forced steps from the IC: energy budget dK/dt = P_inj - eps closes to
+    # the time-integration error (semi-discrete identity at any N)
+    sim.init_field()
+    r0, _, _ = sim.stats()
+    sim.step(2)
+    r1, _, _ = sim.stats()
+    dt = r1["t"] - r0["t"]
+    assert dt > 0 and r1["step"] == 2
+    dK = r1["K"] - r0["K"]
+    src = 0.5 * ((r0["P_inj"] - r0["eps"]) + (r1["P_inj"] - r1["eps"])) * dt
+    assert abs(dK - src) < 0.05 * abs(r0["eps"]) * dt + 1e-6
+    assert abs(r0["cfl"] - 0.5) < 1e-5

@@ -1,0 +1,229 @@
+"""GPU path vs the FP64 oracle, through the C ABI.
+
+Tolerances (relative L2 unless stated): one right-hand side 1e-13 in FP64 and
+2e-6 in FP32-mixed; 20-step trajectories 1e-11 and 1e-4.  Sizes span one and
+several FFT tiles, radix-3 lengths and ragged kx tiles (M not a multiple of the
+column tile)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import psc_oracle as O
+from tests.psc_inputs import compact_to_full, full_to_compact, random_compact_state
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+B = pytest.importorskip("paper_2012_04838_gb300.binding")
+
+TOL_RHS = {B.FP64: 1e-13, B.FP32_MIXED: 2e-6}
+TOL_TRAJ = {B.FP64: 1e-11, B.FP32_MIXED: 1e-4}
+PREC = [B.FP64, B.FP32_MIXED]
+PNAME = {B.FP64: "fp64", B.FP32_MIXED: "fp32"}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+def oparams(p: "B.Params") -> O.Params:
+    return O.Params(N=p.N, nu=p.nu, Sc=p.Sc, beta=p.beta, forcing=p.forcing, kF=p.kF,
+                    eps_inj=p.eps_inj, dt=p.dt, cfl=p.cfl, seed=p.seed, ic=p.ic,
+                    ic_energy=p.ic_energy, ic_noise_frac=p.ic_noise_frac,
+                    integrator=p.integrator, scalar_on=p.scalar_on, record_every=p.record_every)
+
+
+def oracle_rhs(x, p):
+    N = p.N
+    op = oparams(p)
+    g = O.Grid(N)
+    f = compact_to_full(x, N)
+    ru, rp = O.rhs_nonlinear(f[:3], f[3], g, op)
+    if p.integrator == B.INTEG_RK4:
+        Lu, Lp = O.linear_rates(g, op)
+        ru = [ru[c] + Lu * f[c] for c in range(3)]
+        rp = rp + Lp * f[3]
+    return full_to_compact(np.array(list(ru) + [rp]), N)
+
+
+def as_input(x, prec):
+    """The state the GPU sees (rounded to FP32 in mixed mode) as complex128."""
+    if prec == B.FP32_MIXED:
+        return x.astype(np.complex64).astype(np.complex128)
+    return x
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.load()
+    return torch.device("cuda:0")
+
+
+# ---------------------------------------------------------------- right-hand side
+
+@pytest.mark.parametrize("prec", PREC, ids=PNAME.get)
+@pytest.mark.parametrize("N", [8, 12, 16, 24, 32, 48, 64, 96])
+def test_rhs_matches_oracle(dev, N, prec):
+    p = B.Params(N=N, precision=prec, nu=0.013, Sc=0.7, beta=1.1, eps_inj=0.1, kF=2.0)
+    sim = B.Simulation(p, device=dev)
+    x = as_input(random_compact_state(N, 100 + N), prec)
+    got = sim.rhs(torch.from_numpy(x).to(dev)).cpu().numpy().astype(np.complex128)
+    ref = oracle_rhs(x, p)
+    assert rel(got, ref) < TOL_RHS[prec]
+    # each field separately, so no field hides behind a larger one
+    for f in range(4):
+        assert rel(got[f], ref[f]) < 10 * TOL_RHS[prec]
+
+
+@pytest.mark.parametrize("prec", PREC, ids=PNAME.get)
+@pytest.mark.parametrize("N", [128, 192, 256])
+def test_rhs_matches_oracle_large(dev, N, prec):
+    p = B.Params(N=N, precision=prec, nu=0.002, beta=1.0)
+    sim = B.Simulation(p, device=dev)
+    x = as_input(random_compact_state(N, 7 + N, kpeak=8.0), prec)
+    got = sim.rhs(torch.from_numpy(x).to(dev)).cpu().numpy().astype(np.complex128)
+    ref = oracle_rhs(x, p)
+    assert rel(got, ref) < TOL_RHS[prec]
+
+
+@pytest.mark.parametrize("prec", PREC, ids=PNAME.get)
+def test_rhs_plain_rk4_includes_linear_terms(dev, prec):
+    N = 24
+    p = B.Params(N=N, precision=prec, integrator=B.INTEG_RK4, nu=0.05, Sc=2.0)
+    sim = B.Simulation(p, device=dev)
+    x = as_input(random_compact_state(N, 5), prec)
+    got = sim.rhs(torch.from_numpy(x).to(dev)).cpu().numpy().astype(np.complex128)
+    assert rel(got, oracle_rhs(x, p)) < TOL_RHS[prec]
+
+
+@pytest.mark.parametrize("prec", PREC, ids=PNAME.get)
+def test_rhs_edge_cases(dev, prec):
+    N = 16
+    p = B.Params(N=N, precision=prec)
+    sim = B.Simulation(p, device=dev)
+    # zero state: zero right-hand side (forcing amplitude 0 when the band is empty)
+    z = np.zeros(B.compact_shape(N), dtype=np.complex128)
+    got = sim.rhs(torch.from_numpy(z).to(dev)).cpu().numpy()
+    assert np.abs(got).max() == 0.0
+    # only modes outside the forcing band, no scalar: pure nonlinear term
+    x = as_input(random_compact_state(N, 9), prec)
+    K = (N - 1) // 3
+    x[:, K - 2:K + 3, K - 2:K + 3, :3] = 0.0
+    p2 = B.Params(N=N, precision=prec, forcing=B.FORCE_NONE, scalar_on=0)
+    sim2 = B.Simulation(p2, device=dev)
+    got = sim2.rhs(torch.from_numpy(x).to(dev)).cpu().numpy().astype(np.complex128)
+    ref = oracle_rhs(x, p2)
+    assert rel(got, ref) < TOL_RHS[prec]
+    assert np.abs(got[3]).max() == 0.0
+
+
+# ---------------------------------------------------------------- initial condition
+
+@pytest.mark.parametrize("prec", PREC, ids=PNAME.get)
+@pytest.mark.parametrize("N,ic", [(16, B.IC_SPECTRUM_K4), (32, B.IC_TAYLOR_GREEN_NOISE),
+                                  (48, B.IC_PAPER_EQ9), (64, B.IC_SPECTRUM_K4)])
+def test_initial_condition_matches_oracle(dev, N, ic, prec):
+    p = B.Params(N=N, precision=prec, ic=ic, seed=11 + N, ic_energy=1.5, ic_noise_frac=0.01)
+    sim = B.Simulation(p, device=dev)
+    sim.init_field()
+    got = sim.get_state().cpu().numpy().astype(np.complex128)
+    g = O.Grid(N)
+    uh, ph = O.init_field(g, oparams(p))
+    ref = full_to_compact(np.concatenate([uh, ph[None]]), N)
+    assert rel(got, ref) < (1e-13 if prec == B.FP64 else 1e-6)
+    assert np.abs(got[3]).max() == 0.0
+
+
+# ---------------------------------------------------------------- trajectories
+
+@pytest.mark.parametrize("prec", PREC, ids=PNAME.get)
+@pytest.mark.parametrize("N,integ", [(32, B.INTEG_IFRK4), (24, B.INTEG_RK4), (48, B.INTEG_IFRK4)])
+def test_20_step_trajectory_matches_oracle(dev, N, integ, prec):
+    # the 32^3 Taylor-Green case: nu = 0.02, Sc = 1, beta = 1, eps_inj = 0.1 on |k| <= 2
+    p = B.Params(N=N, precision=prec, integrator=integ, nu=0.02, dt=0.005,
+                 ic=B.IC_TAYLOR_GREEN_NOISE, seed=1)
+    sim = B.Simulation(p, device=dev)
+    sim.init_field()
+    sim.step(20)
+    got = sim.get_state().cpu().numpy().astype(np.complex128)
+    op = oparams(p)
+    uh, ph, _, t, _ = O.run(op, 20, with_records=False)
+    ref = full_to_compact(np.concatenate([uh, ph[None]]), N)
+    assert rel(got[:3], ref[:3]) < TOL_TRAJ[prec]
+    assert rel(got[3], ref[3]) < TOL_TRAJ[prec]
+    tt, nstep, _ = sim.time()
+    assert nstep == 20 and abs(tt - t) < 1e-12
+
+
+@pytest.mark.parametrize("prec", PREC, ids=PNAME.get)
+def test_cfl_controlled_run_matches_oracle(dev, prec):
+    N = 32
+    p = B.Params(N=N, precision=prec, nu=0.01, cfl=0.5, record_every=5, ic=B.IC_SPECTRUM_K4,
+                 seed=2, ic_energy=1.5)
+    sim = B.Simulation(p, device=dev)
+    sim.init_field()
+    sim.step(12)
+    got = sim.get_state().cpu().numpy().astype(np.complex128)
+    uh, ph, _, t, dt = O.run(oparams(p), 12, with_records=False)
+    ref = full_to_compact(np.concatenate([uh, ph[None]]), N)
+    assert rel(got, ref) < TOL_TRAJ[prec]
+    tt, _, gdt = sim.time()
+    assert abs(gdt - dt) < (1e-13 if prec == B.FP64 else 1e-6) * dt
+    assert abs(tt - t) < (1e-12 if prec == B.FP64 else 1e-6) * t
+
+
+# ---------------------------------------------------------------- statistics
+
+SCALARS = ["K", "K_phys", "eps", "eps_phys", "eta", "Re_lambda", "urms", "l0", "Te", "umax",
+           "phi_var", "phi_prod", "phi_prod_phys", "chi", "chi_phys", "A", "E_forced", "P_inj"]
+
+
+@pytest.mark.parametrize("prec", PREC, ids=PNAME.get)
+@pytest.mark.parametrize("N", [24, 32])
+def test_stats_match_oracle(dev, N, prec):
+    p = B.Params(N=N, precision=prec, nu=0.02, Sc=0.7, beta=1.0, dt=0.005, ic=B.IC_SPECTRUM_K4, seed=4)
+    sim = B.Simulation(p, device=dev)
+    sim.init_field()
+    sim.step(10)  # develop a scalar field
+    rec, E, Ep = sim.stats()
+    st = sim.get_state().cpu().numpy().astype(np.complex128)
+    f = compact_to_full(st, N)
+    op = oparams(p)
+    ref = O.stats(f[:3], f[3], O.Grid(N), op, rec["t"], rec["dt"])
+    tol = 1e-11 if prec == B.FP64 else 2e-5
+    assert np.allclose(E, ref["E"], rtol=tol, atol=tol * ref["E"].max())
+    assert np.allclose(Ep, ref["Ephi"], rtol=tol, atol=tol * ref["Ephi"].max())
+    for k in SCALARS:
+        assert abs(rec[k] - ref[k]) <= tol * abs(ref[k]) + 1e-300, (k, rec[k], ref[k])
+    atol = 1e-10 if prec == B.FP64 else 1e-4
+    for k in ("skew", "flat", "skew_phi", "flat_phi"):
+        assert np.allclose(rec[k], ref[k], rtol=atol, atol=atol), (k, rec[k], ref[k])
+    assert rec["step"] == 10
+
+
+# ---------------------------------------------------------------- state round trip
+
+@pytest.mark.parametrize("prec", PREC, ids=PNAME.get)
+def test_state_roundtrip_and_restart_are_bit_exact(dev, prec):
+    N = 32
+    p = B.Params(N=N, precision=prec, ic=B.IC_SPECTRUM_K4, seed=3, dt=0.004)
+    a = B.Simulation(p, device=dev)
+    a.init_field()
+    a.step(5)
+    mid = a.get_state(device="cpu")
+    a.step(5)
+    end_a = a.get_state().cpu()
+    b = B.Simulation(p, device=dev)
+    b.set_state(mid)
+    assert torch.equal(b.get_state(device="cpu"), mid)
+    # dt and t are part of the run, not of the state: restart from step 5 with the same dt
+    b.step(5)
+    assert torch.equal(b.get_state().cpu(), end_a)
+
+
+def test_unsupported_and_short_workspace(dev):
+    with pytest.raises(B.PscError):
+        B.Simulation(B.Params(N=100), device=dev)

@@ -436,3 +436,32 @@ def test_table1_derived_scales_are_consistent():
     assert abs(s["Re_lambda"] - s["K"] * math.sqrt(20.0 / (3.0 * p.nu * s["eps"]))) < 1e-12 * s["Re_lambda"]
     assert abs(s["l0"] / s["eta"] - s["Re_lambda"] ** 1.5 / 15 ** 0.75) < 1e-10 * s["l0"] / s["eta"]
     assert abs(s["Te"] - s["l0"] / s["urms"]) < 1e-14 * s["Te"]
+
+
+def test_sparse_triad_rhs_matches_fft_rhs():
+    # two independent formulations of the same Galerkin right-hand side
+    N = 24
+    K = (N - 1) // 3
+    p = O.Params(N=N, nu=0.02, beta=0.9, eps_inj=0.1, kF=2.0)
+    rng = np.random.default_rng(3)
+    modes = {}
+    picks = [(1, 0, 1), (0, 2, -1), (2, 1, 0), (K, -K, 3), (3, K, -K), (1, -1, -1), (0, 1, 1)]
+    for k in picks:
+        v = rng.standard_normal(4) + 1j * rng.standard_normal(4)
+        modes[k] = v * N ** 3 * 0.1
+        if k[0] == 0:
+            modes[(0, -k[1], -k[2])] = np.conj(modes[k])
+    full = np.zeros((4,) + O.Grid(N).shape_hat, dtype=np.complex128)
+    for (kx, ky, kz), v in modes.items():
+        full[:, kz % N, ky % N, kx] = v
+    g = O.Grid(N)
+    ru, rp = O.rhs_nonlinear(full[:3], full[3], g, p)
+    ref = np.array(list(ru) + [rp])
+    got = O.rhs_sparse_triads(modes, N, p)
+    scale = np.abs(ref).max()
+    seen = np.zeros(ref.shape[1:], dtype=bool)
+    for (kx, ky, kz), v in got.items():
+        assert np.abs(ref[:, kz % N, ky % N, kx] - v).max() < 1e-11 * scale
+        seen[kz % N, ky % N, kx] = True
+    # every mode the FFT path fills is one the triad sum found
+    assert np.abs(np.where(seen[None], 0, ref)).max() < 1e-11 * scale
