@@ -470,7 +470,8 @@ def target_shell_energy(nmax: int, shape: int, K0: float, kF: float) -> np.ndarr
     (n/kF)^2 for n <= kF and (n/kF)^(-5/3) above.  E(0) = 0."""
     n = np.arange(nmax, dtype=np.float64)
     if shape == IC_PAPER_EQ9:
-        e = np.where(n <= kF, (n / kF) ** 2, (np.maximum(n, 1e-300) / kF) ** (-5.0 / 3.0))
+        safe = np.maximum(n, 1.0)
+        e = np.where(n <= kF, (n / kF) ** 2, (safe / kF) ** (-5.0 / 3.0))
     else:
         e = n ** 4 * np.exp(-2.0 * (n / 4.0) ** 2)
     e[0] = 0.0

@@ -203,6 +203,10 @@ static const PassTable* pick_table(const psc_params* p) {
   return p->precision == PSC_FP64 ? table_f64(p->N) : table_f32(p->N);
 }
 
+namespace {
+template <typename T> void launch_iftab(psc_sim* s);
+}
+
 extern "C" {
 
 const char* psc_last_error(void) { return g_err.c_str(); }
@@ -258,6 +262,12 @@ psc_status psc_create(const psc_params* p, void* dev_ws, size_t ws_bytes, void* 
   else e = cudaMemcpyAsync(sim->ws + L.tw, twf.data(), twf.size() * 4, cudaMemcpyHostToDevice, sim->st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(sim->ctrl, &c0, sizeof(c0), cudaMemcpyHostToDevice, sim->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(sim->ws + L.U, 0, L.V - L.U, sim->st);
+  if (e == cudaSuccess) {
+    // integrating factors for the initial dt, so a state set by psc_set_state can be stepped
+    if (sim->fp64) launch_iftab<double>(sim);
+    else launch_iftab<float>(sim);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(sim->st);
   if (e != cudaSuccess) {
     delete sim;

