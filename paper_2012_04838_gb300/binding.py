@@ -72,6 +72,8 @@ EXPORTS = [
     ("psc_profile_read", ct.c_int, [_VP, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.c_int32]),
     ("psc_launch_count", ct.c_int, [_VP, ct.POINTER(ct.c_int64)]),
     ("psc_destroy", ct.c_int, [_VP]),
+    ("psc_shell_spectra_noalloc", ct.c_int, [_VP, ct.c_int32, ct.c_int32, ct.POINTER(ct.c_double),
+                                             ct.POINTER(ct.c_double), ct.c_int32, _VP]),
     ("psc_last_error", ct.c_char_p, []),
 ]
 

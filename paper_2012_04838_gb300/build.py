@@ -71,8 +71,9 @@ def build(checked: bool | None = None, jobs: int | None = None, verbose: bool = 
             obj = os.path.join(odir, f"inst_{t}_{n}.o")
             units.append((obj, [cc] + flags + [f"-DPSC_INST_T={t}", f"-DPSC_INST_N={n}", "-c",
                                                os.path.join(CSRC, "psc_inst.cu"), "-o", obj]))
-    cap = os.path.join(odir, "psc_capi.o")
-    units.append((cap, [cc] + flags + ["-c", os.path.join(CSRC, "psc_capi.cu"), "-o", cap]))
+    for src in ("psc_capi", "psc_noalloc"):
+        obj = os.path.join(odir, src + ".o")
+        units.append((obj, [cc] + flags + ["-c", os.path.join(CSRC, src + ".cu"), "-o", obj]))
     todo = [(o, c) for o, c in units if not os.path.exists(o)]
     if todo:
         jobs = jobs or max(1, os.cpu_count() or 1)

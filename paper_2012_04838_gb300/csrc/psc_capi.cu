@@ -59,6 +59,8 @@ static psc_status fail(psc_status st, const std::string& msg) {
   g_err = msg;
   return st;
 }
+
+void set_error(const std::string& msg) { g_err = msg; }
 static psc_status cuda_fail(cudaError_t e, const char* where) {
   return fail(PSC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }

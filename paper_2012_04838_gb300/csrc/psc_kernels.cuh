@@ -168,6 +168,7 @@ __global__ void k_iftab(int K, const Ctrl* ctrl, double nu, double D, T* eu, T* 
   ep[k] = (T)exp(-D * (double)k * k * dt * 0.5);
 }
 
+#ifndef PSC_SHELLS_ONLY
 // dt = cfl dx / max(|u1|+|u2|+|u3|)  (Eq. 10); a non-finite maximum raises
 // the instability flag and leaves dt unchanged.
 __global__ void k_cfl(Ctrl* c, double cfl, double dx) {
@@ -176,6 +177,8 @@ __global__ void k_cfl(Ctrl* c, double cfl, double dx) {
   if (!(m <= 1.7976931348623157e308)) { c->err |= 2; return; }
   if (m > 0.0) c->dt = cfl * dx / m;
 }
+
+#endif  // PSC_SHELLS_ONLY
 
 // Fixed-order block sum of one double (every thread passes its value; the
 // result is valid in thread 0).
@@ -249,6 +252,7 @@ __global__ void __launch_bounds__(256) k_shells(Dims d, const void* u_, const vo
   }
 }
 
+#ifndef PSC_SHELLS_ONLY
 // Sum the X-pass partials over warps in a fixed order.
 __global__ void k_reduce_moments(const double* partials, int nw, Ctrl* ctrl) {
   const int q = threadIdx.x;
@@ -364,5 +368,7 @@ __global__ void k_ic_finish(Dims d, const double2* z, const double* fac, int tay
   for (int c = 0; c < 3; ++c) U[c * d.S + i] = mk((T)v[c][0], (T)v[c][1]);
   U[3 * d.S + i] = mk(T(0), T(0));
 }
+
+#endif  // PSC_SHELLS_ONLY
 
 }  // namespace psc
