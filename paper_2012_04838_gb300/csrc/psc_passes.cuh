@@ -31,8 +31,9 @@ namespace psc {
 template <typename T, int N> struct StridedCfg {
   static constexpr int W = (sizeof(T) == 4) ? ((N >= 512) ? 8 : 16) : 8;
   static constexpr int THREADS = W * PlanD<N>::TPL;
-  // cap registers at 128 per thread so at least 512 threads fit on an SM
-  static constexpr int MINB = THREADS >= 512 ? 1 : 512 / THREADS;
+  // FP32: cap registers at 128 per thread so at least 512 threads fit on an SM;
+  // FP64 is bound by the FP64 pipe, so it keeps its values in registers instead
+  static constexpr int MINB = sizeof(T) == 8 ? 1 : (THREADS >= 512 ? 1 : 512 / THREADS);
 };
 
 template <typename T, int N, int W> struct StridedSmem {
@@ -97,6 +98,9 @@ template <int N> __device__ __forceinline__ bool k_of_pos(int p, int& k) {
   return false;
 }
 
+// Each kernel runs its transforms through one copy of the transform code (a
+// runtime loop over its stream table), so the instruction footprint stays that
+// of a single two-step FFT however many streams the pass carries.
 template <typename T, int N, bool STATS>
 __global__ void __launch_bounds__(StridedCfg<T, N>::THREADS, StridedCfg<T, N>::MINB)
 k_zinv(PassArgs a) {
@@ -113,33 +117,39 @@ k_zinv(PassArgs a) {
   const C* __restrict__ tw = static_cast<const C*>(a.tw);
   const long long S = (long long)P * P * M, zs = (long long)N * P * M;
   const C zero = mk(T(0), T(0));
-
-  auto load = [&](int f, int p, bool deriv) -> C {
-    int kz;
-    if (!act || !k_of_pos<N>(p, kz)) return zero;
-    const long long idx = f * S + ((long long)(kz + K) * P + iy) * M + ix;
-    if (!PSC_OK_INDEX(idx, 4 * S, a.ctrl)) return zero;
-    const C v = in[idx];
-    return deriv ? mul_ik(v, T(kz)) : v;
-  };
-  auto run = [&](int f, bool deriv, int s) {
+  // (input field, multiply by i kz, output stream)
+  constexpr int nt = STATS ? 8 : 7;
+#pragma unroll 1
+  for (int tr = 0; tr < nt; ++tr) {
+    int f, s;
+    bool deriv;
+    switch (tr) {
+      case 0: f = 0; deriv = false; s = Z_UX; break;
+      case 1: f = 1; deriv = false; s = Z_UY; break;
+      case 2: f = 2; deriv = false; s = Z_UZ; break;
+      case 3: f = 1; deriv = true; s = Z_DZUY; break;
+      case 4: f = 0; deriv = true; s = Z_DZUX; break;
+      case 5: f = 3; deriv = false; s = Z_PHI; break;
+      case 6: f = 3; deriv = true; s = Z_DZPHI; break;
+      default: f = 2; deriv = true; s = Z_DZUZ; break;
+    }
+    const C* __restrict__ src = in + f * S + (long long)iy * M + ix;
     strided_fft<T, N, W, +1>(
-        [&](int p) { return load(f, p, deriv); },
+        [&](int p) -> C {
+          int kz;
+          if (!act || !k_of_pos<N>(p, kz)) return zero;
+          const long long off = (long long)(kz + K) * P * M;
+          if (!PSC_OK_INDEX(f * S + off + (long long)iy * M + ix, 4 * S, a.ctrl)) return zero;
+          const C v = src[off];
+          return deriv ? mul_ik(v, T(kz)) : v;
+        },
         [&](int z, C v) {
           if (!act) return;
           const long long idx = s * zs + ((long long)z * P + iy) * M + ix;
           if (PSC_OK_INDEX(idx, (long long)Z_NSTREAM * zs, a.ctrl)) zb[idx] = v;
         },
         sm, tw, t, w);
-  };
-  run(0, false, Z_UX);
-  run(1, false, Z_UY);
-  run(2, false, Z_UZ);
-  run(1, true, Z_DZUY);
-  run(0, true, Z_DZUX);
-  run(3, false, Z_PHI);
-  run(3, true, Z_DZPHI);
-  if (STATS) run(2, true, Z_DZUZ);
+  }
 }
 
 template <typename T, int N, bool STATS>
@@ -158,21 +168,37 @@ k_yinv(PassArgs a) {
   const C* __restrict__ tw = static_cast<const C*>(a.tw);
   const long long zs = (long long)N * P * M, ys = (long long)N * N * M;
   const C zero = mk(T(0), T(0));
-
-  auto zl = [&](int s, int ky) -> C {
-    const long long idx = s * zs + ((long long)z * P + (ky + K)) * M + ix;
-    if (!PSC_OK_INDEX(idx, (long long)Z_NSTREAM * zs, a.ctrl)) return zero;
-    return zb[idx];
-  };
-  // kind 0: stream s1; 1: i ky s1; 2: i ky s1 - s2
-  auto run = [&](int kind, int s1, int s2, int so) {
+  // (kind, s1, s2, out): kind 0 = s1, 1 = i ky s1, 2 = i ky s1 - s2
+  constexpr int nt = STATS ? 11 : 9;
+#pragma unroll 1
+  for (int tr = 0; tr < nt; ++tr) {
+    int kind, s1, s2 = 0, so;
+    switch (tr) {
+      case 0: kind = 0; s1 = Z_UX; so = Y_UX; break;
+      case 1: kind = 0; s1 = Z_UY; so = Y_UY; break;
+      case 2: kind = 0; s1 = Z_UZ; so = Y_UZ; break;
+      case 3: kind = 2; s1 = Z_UZ; s2 = Z_DZUY; so = Y_WX; break;  // omega_x = d_y u_z - d_z u_y
+      case 4: kind = 0; s1 = Z_DZUX; so = Y_DZUX; break;
+      case 5: kind = 1; s1 = Z_UX; so = Y_DYUX; break;
+      case 6: kind = 0; s1 = Z_PHI; so = Y_PHI; break;
+      case 7: kind = 1; s1 = Z_PHI; so = Y_DYPHI; break;
+      case 8: kind = 0; s1 = Z_DZPHI; so = Y_DZPHI; break;
+      case 9: kind = 1; s1 = Z_UY; so = Y_DYUY; break;
+      default: kind = 0; s1 = Z_DZUZ; so = Y_DZUZ; break;
+    }
+    const long long rowz = (long long)z * P * M + ix;
     strided_fft<T, N, W, +1>(
         [&](int p) -> C {
           int ky;
           if (!act || !k_of_pos<N>(p, ky)) return zero;
-          if (kind == 0) return zl(s1, ky);
-          const C d = mul_ik(zl(s1, ky), T(ky));
-          return kind == 1 ? d : csub(d, zl(s2, ky));
+          const long long o = rowz + (long long)(ky + K) * M;
+          if (!PSC_OK_INDEX(s1 * zs + o, (long long)Z_NSTREAM * zs, a.ctrl)) return zero;
+          const C v1 = zb[s1 * zs + o];
+          if (kind == 0) return v1;
+          const C d = mul_ik(v1, T(ky));
+          if (kind == 1) return d;
+          if (!PSC_OK_INDEX(s2 * zs + o, (long long)Z_NSTREAM * zs, a.ctrl)) return zero;
+          return csub(d, zb[s2 * zs + o]);
         },
         [&](int y, C v) {
           if (!act) return;
@@ -180,19 +206,6 @@ k_yinv(PassArgs a) {
           if (PSC_OK_INDEX(idx, (long long)Y_NSTREAM * ys, a.ctrl)) yb[idx] = v;
         },
         sm, tw, t, w);
-  };
-  run(0, Z_UX, 0, Y_UX);
-  run(0, Z_UY, 0, Y_UY);
-  run(0, Z_UZ, 0, Y_UZ);
-  run(2, Z_UZ, Z_DZUY, Y_WX);      // omega_x = d_y u_z - d_z u_y
-  run(0, Z_DZUX, 0, Y_DZUX);
-  run(1, Z_UX, 0, Y_DYUX);
-  run(0, Z_PHI, 0, Y_PHI);
-  run(1, Z_PHI, 0, Y_DYPHI);
-  run(0, Z_DZPHI, 0, Y_DZPHI);
-  if (STATS) {
-    run(1, Z_UY, 0, Y_DYUY);
-    run(0, Z_DZUZ, 0, Y_DZUZ);
   }
 }
 
