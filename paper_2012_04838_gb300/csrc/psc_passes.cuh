@@ -653,6 +653,12 @@ k_xpass(PassArgs a) {
   }
 }
 
+}  // namespace psc
+
+#include "psc_xpass2.cuh"
+
+namespace psc {
+
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
@@ -663,11 +669,20 @@ template <typename T, int N> struct Passes {
   static constexpr int M = PlanD<N>::M, P = PlanD<N>::P;
   static constexpr size_t SSM = StridedSmem<T, N, W>::BYTES;
 
+  // rows of N = 512 and 1024 use the 16-values-per-thread layout of psc_xpass2.cuh
+  static constexpr bool X2 = (N == 512 || N == 1024);
+
   static int xgrid() {
-    const long long groups = ((long long)N * N + XCfg<T, N>::LPW - 1) / XCfg<T, N>::LPW;
-    long long g = (groups + XCfg<T, N>::WARPS - 1) / XCfg<T, N>::WARPS;
-    const long long cap = 152 * 8;
-    return (int)(g < cap ? g : cap);
+    if constexpr (X2) {
+      const long long g = (long long)N * N / X2Cfg<T, N>::ROWS;
+      const long long cap = 152 * 16;
+      return (int)(g < cap ? g : cap);
+    } else {
+      const long long groups = ((long long)N * N + XCfg<T, N>::LPW - 1) / XCfg<T, N>::LPW;
+      long long g = (groups + XCfg<T, N>::WARPS - 1) / XCfg<T, N>::WARPS;
+      const long long cap = 152 * 8;
+      return (int)(g < cap ? g : cap);
+    }
   }
 
   template <class KER> static void prep(KER k, size_t smem) {
@@ -685,6 +700,17 @@ template <typename T, int N> struct Passes {
     else { prep(k_yinv<T, N, false>, SSM); k_yinv<T, N, false><<<grid, block, SSM, a.st>>>(a); }
   }
   static void xpass(const PassArgs& a, int mode) {
+    if constexpr (X2) {
+      const size_t sm2 = X2Cfg<T, N>::SMEM;
+      if (mode == XMODE_STATS) {
+        prep(k_xpass2<T, N, XMODE_STATS>, sm2);
+        k_xpass2<T, N, XMODE_STATS><<<xgrid(), 128, sm2, a.st>>>(a);
+      } else {
+        prep(k_xpass2<T, N, XMODE_RHS>, sm2);
+        k_xpass2<T, N, XMODE_RHS><<<xgrid(), 128, sm2, a.st>>>(a);
+      }
+      return;
+    }
     const size_t sm = XCfg<T, N>::SMEM;
     dim3 block(32 * XCfg<T, N>::WARPS);
     if (mode == XMODE_STATS) {
@@ -706,7 +732,8 @@ template <typename T, int N> struct Passes {
     k_zfwd<T, N><<<grid, block, SSM, a.st>>>(a);
   }
   static const PassTable* table() {
-    static const PassTable tb = {&zinv, &yinv, &xpass, &yfwd, &zfwd, xgrid() * XCfg<T, N>::WARPS};
+    static const PassTable tb = {&zinv, &yinv, &xpass, &yfwd, &zfwd,
+                                 xgrid() * (X2 ? 4 : XCfg<T, N>::WARPS)};
     return &tb;
   }
 };

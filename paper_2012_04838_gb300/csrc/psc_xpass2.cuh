@@ -1,0 +1,377 @@
+// X pass for N = 16 * 16 * G (G = 2: N = 512, G = 4: N = 1024).
+//
+// One row of N points is transformed by TH = 16 G threads holding 16 values
+// each.  With n = a + 16 b + 256 c and k = k0 + G k1 + 16 G k2
+// (a, b, k1, k2 < 16; c, k0 < G) the DFT factors into
+//   X[k] = sum_a w16^(a k2) wN^(a (k0 + G k1)) sum_b w16^(b k1) wN^(16 b k0)
+//          sum_c wG^(c k0) x[a + 16 b + 256 c],
+// so a transform is: a DFT of size G across G adjacent lanes (shuffles), a
+// DFT-16 in registers, one exchange through shared memory, a second DFT-16.
+// The inverse runs the same steps in the opposite order, which leaves every
+// physical value on the lane and register the forward transform starts from:
+// thread (a, r) holds x[a + 16 b + 256 r], b < 16, for every field, so the
+// products u x omega and u . grad phi are formed in registers and no field is
+// parked in shared memory.  Registers per thread stay near a hundred, which
+// keeps 4x more rows in flight per SM than one warp per row of 32 values.
+#pragma once
+
+#include "psc_common.cuh"
+
+namespace psc {
+
+template <typename T, int N> struct X2Cfg {
+  using C = typename CT<T>::type;
+  static constexpr int G = N / 256;
+  static constexpr int TH = 16 * G;      // threads per row
+  static constexpr int ROWS = 128 / TH;  // rows per 128-thread CTA
+  // exchange rows of 16 G values padded to 17 G: the (a, k0 + G k1) accesses
+  // of 32 lanes then fall in distinct bank groups
+  static constexpr int ROW = 17 * G;
+  static constexpr int EXCH = 16 * ROW > N ? 16 * ROW : N;
+  static constexpr size_t LINE_BYTES = (EXCH * sizeof(C) + 15) / 16 * 16;
+  static constexpr size_t ACC_BYTES = 4 * NQ * sizeof(double);
+  static constexpr size_t SMEM = LINE_BYTES * ROWS + ACC_BYTES;
+  static constexpr int K = (N - 1) / 3;
+  static_assert(N == 512 || N == 1024, "X2 layout covers N = 512 and 1024");
+};
+
+// barrier over the TH threads of one row
+template <int TH> __device__ __forceinline__ void row_sync(int id) {
+  if constexpr (TH == 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(TH) : "memory");
+  }
+}
+
+template <int G> __device__ __forceinline__ int bitrev_lane(int r) {
+  if constexpr (G == 4) return ((r & 1) << 1) | (r >> 1);
+  else return r;
+}
+
+// DFT of size G across the G adjacent lanes of a group, element-wise on v.
+// Forward (DIR = -1): lane r holds input c = r and ends with output k0 = bitrev(r).
+// Inverse (DIR = +1): lane r holds input k0 = bitrev(r) and ends with c = r.
+template <typename T, int G, int DIR>
+__device__ __forceinline__ void lane_dft(typename CT<T>::type (&v)[16], int r) {
+  using C = typename CT<T>::type;
+  auto bfly = [&](int mask, bool upper) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const C o = mk(__shfl_xor_sync(0xffffffffu, v[i].x, mask), __shfl_xor_sync(0xffffffffu, v[i].y, mask));
+      v[i] = upper ? csub(o, v[i]) : cadd(v[i], o);
+    }
+  };
+  auto quarter = [&]() {  // multiply by exp(DIR * 2 pi i / 4) on the lane with both bits set
+    if (r == 3) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = DIR < 0 ? mk(v[i].y, -v[i].x) : mk(-v[i].y, v[i].x);
+    }
+  };
+  if constexpr (G == 2) {
+    bfly(1, r & 1);
+  } else if constexpr (DIR < 0) {
+    bfly(2, r & 2);
+    quarter();
+    bfly(1, r & 1);
+  } else {
+    bfly(1, r & 1);
+    quarter();
+    bfly(2, r & 2);
+  }
+}
+
+struct X2Roles {
+  int tid;  // thread within the row: inverse input / forward output column j
+  int ra;   // a of the (a, r) role
+  int rr;   // r of the (a, r) role (lane within the G-group)
+  int rk0;  // k0 held by lane rr between the lane DFT and the DFT-16 over b
+  int bar;  // named barrier of this row
+};
+
+// Inverse transform of a Hermitian-packed half spectrum (two real fields):
+// Z[p] = X1[p] + i X2[p] (p <= K, imaginary parts dropped at p = 0),
+// conj(X1[N-p]) + i conj(X2[N-p]) (p >= N-K), 0 elsewhere.  On return
+// z[b] = scale * IDFT(Z) at n = ra + 16 b + 256 rr.
+template <typename T, int N, class SPEC>
+__device__ __forceinline__ void x2inv(const SPEC& spec, typename CT<T>::type (&z)[16],
+                                      typename CT<T>::type* ex,
+                                      const typename CT<T>::type* __restrict__ tw, const X2Roles& q,
+                                      T scale) {
+  using C = typename CT<T>::type;
+  using XC = X2Cfg<T, N>;
+  constexpr int TH = XC::TH, G = XC::G, ROW = XC::ROW, K = XC::K;
+  C v[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int p = q.tid + TH * m;
+    C x1, x2;
+    if (p <= K) {
+      spec(p, x1, x2);
+      if (p == 0) { x1.y = T(0); x2.y = T(0); }
+      v[m] = mk(x1.x - x2.y, x1.y + x2.x);
+    } else if (p >= N - K) {
+      spec(N - p, x1, x2);
+      v[m] = mk(x1.x + x2.y, x2.x - x1.y);
+    } else {
+      v[m] = mk(T(0), T(0));
+    }
+  }
+  Dft<16, +1>::template run<T, C>(v);  // over k2 -> a
+#pragma unroll
+  for (int a = 0; a < 16; ++a) {
+    C w = v[a];
+    if (a > 0) w = cmulc(w, tw[a * q.tid]);  // wN^(-a j)
+    ex[a * ROW + q.tid] = w;
+  }
+  row_sync<TH>(q.bar);
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) z[k1] = ex[q.ra * ROW + q.rk0 + G * k1];
+  row_sync<TH>(q.bar);
+  Dft<16, +1>::template run<T, C>(z);  // over k1 -> b
+  if (q.rk0 > 0) {
+#pragma unroll
+    for (int b = 1; b < 16; ++b) z[b] = cmulc(z[b], tw[16 * b * q.rk0]);  // wN^(-16 b k0)
+  }
+  lane_dft<T, G, +1>(z, q.rr);  // over k0 -> c
+#pragma unroll
+  for (int b = 0; b < 16; ++b) z[b] = cscale(z[b], scale);
+}
+
+// Forward transform of two real fields packed as x1 + i x2 at the positions
+// x2inv leaves them in; out(kx, X1, X2) receives both half spectra for kx <= K.
+template <typename T, int N, class OUT>
+__device__ __forceinline__ void x2fwd(typename CT<T>::type (&z)[16], const OUT& out,
+                                      typename CT<T>::type* ex,
+                                      const typename CT<T>::type* __restrict__ tw, const X2Roles& q) {
+  using C = typename CT<T>::type;
+  using XC = X2Cfg<T, N>;
+  constexpr int TH = XC::TH, G = XC::G, ROW = XC::ROW, K = XC::K;
+  lane_dft<T, G, -1>(z, q.rr);  // over c -> k0
+  if (q.rk0 > 0) {
+#pragma unroll
+    for (int b = 1; b < 16; ++b) z[b] = cmul(z[b], tw[16 * b * q.rk0]);  // wN^(16 b k0)
+  }
+  Dft<16, -1>::template run<T, C>(z);  // over b -> k1
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) {
+    const int j = q.rk0 + G * k1;
+    C w = z[k1];
+    if (q.ra > 0 && j > 0) w = cmul(w, tw[q.ra * j]);  // wN^(a (k0 + G k1))
+    ex[q.ra * ROW + j] = w;
+  }
+  row_sync<TH>(q.bar);
+  C v[16];
+#pragma unroll
+  for (int a = 0; a < 16; ++a) v[a] = ex[a * ROW + q.tid];
+  row_sync<TH>(q.bar);
+  Dft<16, -1>::template run<T, C>(v);  // over a -> k2
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) ex[q.tid + TH * k2] = v[k2];  // natural order
+  row_sync<TH>(q.bar);
+  for (int kx = q.tid; kx <= K; kx += TH) {
+    const C A = ex[kx];
+    const C B = ex[kx == 0 ? 0 : N - kx];
+    out(kx, mk(T(0.5) * (A.x + B.x), T(0.5) * (A.y - B.y)),
+        mk(T(0.5) * (A.y + B.y), T(0.5) * (B.x - A.x)));
+  }
+  row_sync<TH>(q.bar);
+}
+
+template <typename T>
+__device__ __forceinline__ double warp_sum_d(T v) {
+  double d = (double)v;
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+  return d;
+}
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(128, 3) k_xpass2(PassArgs a) {
+  using C = typename CT<T>::type;
+  using XC = X2Cfg<T, N>;
+  constexpr int TH = XC::TH, G = XC::G, ROWS = XC::ROWS, M = XC::K + 1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int lid = threadIdx.x / TH;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  X2Roles q;
+  q.tid = threadIdx.x % TH;
+  q.ra = q.tid / G;
+  q.rr = q.tid % G;
+  q.rk0 = bitrev_lane<G>(q.rr);
+  q.bar = 1 + lid;
+  C* ex = reinterpret_cast<C*>(smraw + (size_t)lid * XC::LINE_BYTES);
+  double* accw = reinterpret_cast<double*>(smraw + XC::LINE_BYTES * ROWS) + wid * NQ;
+  const C* __restrict__ yb = static_cast<const C*>(a.yb);
+  C* __restrict__ xb = static_cast<C*>(a.xb);
+  const C* __restrict__ tw = static_cast<const C*>(a.tw);
+  const long long ys = (long long)N * N * M;
+  const long long nlines = (long long)N * N;
+  const T scale = T(1.0 / ((double)N * N * N));
+  const C zero = mk(T(0), T(0));
+  double umax = 0.0;
+  if (MODE == XMODE_STATS) {
+    for (int i = lane; i < NQ; i += 32) accw[i] = 0.0;
+    __syncwarp();
+  }
+
+#pragma unroll 1
+  for (long long base = (long long)blockIdx.x * ROWS; base < nlines; base += (long long)gridDim.x * ROWS) {
+    const long long line = base + lid;  // N*N is a multiple of ROWS
+    const C* __restrict__ row = yb + line * M;
+    auto Y = [&](int s, int kx) -> C {
+      if (!PSC_OK_INDEX(s * ys + line * M + kx, (long long)Y_NSTREAM * ys, a.ctrl)) return zero;
+      return row[s * ys + kx];
+    };
+    C z[16];
+    if constexpr (MODE == XMODE_RHS) {
+      T u1[16], u2[16], u3[16], A1[16], A2[16];
+      // (u1, u2)
+      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UY, kx); }, z, ex, tw, q, scale);
+#pragma unroll
+      for (int b = 0; b < 16; ++b) { u1[b] = z[b].x; u2[b] = z[b].y; }
+      // (u3, omega1)
+      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UZ, kx); x2 = Y(Y_WX, kx); }, z, ex, tw, q, scale);
+#pragma unroll
+      for (int b = 0; b < 16; ++b) {
+        u3[b] = z[b].x;
+        A1[b] = z[b].x * z[b].y;    // u3 omega1 (part of NL2)
+        A2[b] = -u2[b] * z[b].y;    // -u2 omega1 (part of NL3)
+        if (a.want_umax) {
+          const double s3 = (double)(fabs(u1[b]) + fabs(u2[b]) + fabs(u3[b]));
+          umax = s3 > umax || s3 != s3 ? s3 : umax;
+        }
+      }
+      // (omega2, omega3): omega2 = d_z u1 - i kx u3, omega3 = i kx u2 - d_y u1
+      x2inv<T, N>(
+          [&](int kx, C& x1, C& x2) {
+            x1 = csub(Y(Y_DZUX, kx), mul_ik(Y(Y_UZ, kx), T(kx)));
+            x2 = csub(mul_ik(Y(Y_UY, kx), T(kx)), Y(Y_DYUX, kx));
+          },
+          z, ex, tw, q, scale);
+#pragma unroll
+      for (int b = 0; b < 16; ++b) {
+        const T w2 = z[b].x, w3 = z[b].y;
+        z[b] = mk(u2[b] * w3 - u3[b] * w2, A1[b] - u1[b] * w3);  // (NL1, NL2)
+        A2[b] += u1[b] * w2;                                     // NL3
+      }
+      x2fwd<T, N>(z,
+                  [&](int kx, C X1, C X2) {
+                    const long long i0 = line * M + kx;
+                    if (PSC_OK_INDEX(i0 + ys, 4 * ys, a.ctrl)) { xb[i0] = X1; xb[i0 + ys] = X2; }
+                  },
+                  ex, tw, q);
+      // (dphi/dx1, dphi/dx2)
+      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_PHI, kx), T(kx)); x2 = Y(Y_DYPHI, kx); },
+                  z, ex, tw, q, scale);
+#pragma unroll
+      for (int b = 0; b < 16; ++b) A1[b] = u1[b] * z[b].x + u2[b] * z[b].y;
+      // (dphi/dx3, 0)
+      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZPHI, kx); x2 = zero; }, z, ex, tw, q, scale);
+#pragma unroll
+      for (int b = 0; b < 16; ++b) z[b] = mk(A2[b], A1[b] + u3[b] * z[b].x);  // (NL3, u.grad phi)
+      x2fwd<T, N>(z,
+                  [&](int kx, C X1, C X2) {
+                    const long long i0 = 2 * ys + line * M + kx;
+                    if (PSC_OK_INDEX(i0 + ys, 4 * ys, a.ctrl)) { xb[i0] = X1; xb[i0 + ys] = X2; }
+                  },
+                  ex, tw, q);
+    } else {
+      // statistics (Eqs. 11-13): per pair, FP32/FP64 partial sums of the thread's
+      // 16 points, reduced over the warp in FP64 into the warp's accumulators
+      T s13[16];
+      auto put = [&](int slot, T v) {
+        const double d = warp_sum_d<T>(v);
+        if (lane == 0) accw[slot] += d;
+      };
+      auto mom3 = [&](int slot, const T (&f)[16]) {
+        T m2 = T(0), m3 = T(0), m4 = T(0);
+#pragma unroll
+        for (int b = 0; b < 16; ++b) { const T v2 = f[b] * f[b]; m2 += v2; m3 += v2 * f[b]; m4 += v2 * v2; }
+        put(slot, m2); put(slot + 1, m3); put(slot + 2, m4);
+      };
+      T f1[16], f2[16];
+      auto split = [&]() {
+#pragma unroll
+        for (int b = 0; b < 16; ++b) { f1[b] = z[b].x; f2[b] = z[b].y; }
+      };
+      // (u1, u3)
+      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UZ, kx); }, z, ex, tw, q, scale);
+      split();
+      {
+        T s = T(0);
+#pragma unroll
+        for (int b = 0; b < 16; ++b) { s += f1[b] * f1[b] + f2[b] * f2[b]; s13[b] = fabs(f1[b]) + fabs(f2[b]); }
+        put(0, s);
+      }
+      // (u2, phi)
+      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UY, kx); x2 = Y(Y_PHI, kx); }, z, ex, tw, q, scale);
+      split();
+      {
+        T s0 = T(0), s1 = T(0), s2 = T(0);
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+          s0 += f1[b] * f1[b]; s1 += f2[b] * f1[b]; s2 += f2[b] * f2[b];
+          const double s3 = (double)(s13[b] + fabs(f1[b]));
+          umax = s3 > umax || s3 != s3 ? s3 : umax;
+        }
+        put(0, s0); put(20, s1); put(21, s2);
+      }
+      // (omega1, omega2)
+      x2inv<T, N>(
+          [&](int kx, C& x1, C& x2) { x1 = Y(Y_WX, kx); x2 = csub(Y(Y_DZUX, kx), mul_ik(Y(Y_UZ, kx), T(kx))); },
+          z, ex, tw, q, scale);
+      split();
+      {
+        T s = T(0);
+#pragma unroll
+        for (int b = 0; b < 16; ++b) s += f1[b] * f1[b] + f2[b] * f2[b];
+        put(1, s);
+      }
+      // (omega3, dphi/dx1)
+      x2inv<T, N>(
+          [&](int kx, C& x1, C& x2) {
+            x1 = csub(mul_ik(Y(Y_UY, kx), T(kx)), Y(Y_DYUX, kx));
+            x2 = mul_ik(Y(Y_PHI, kx), T(kx));
+          },
+          z, ex, tw, q, scale);
+      split();
+      {
+        T s = T(0);
+#pragma unroll
+        for (int b = 0; b < 16; ++b) s += f1[b] * f1[b];
+        put(1, s);
+        mom3(11, f2);
+      }
+      // (dphi/dx2, dphi/dx3)
+      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DYPHI, kx); x2 = Y(Y_DZPHI, kx); }, z, ex, tw, q, scale);
+      split();
+      mom3(14, f1);
+      mom3(17, f2);
+      // (du1/dx1, du2/dx2)
+      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_UX, kx), T(kx)); x2 = Y(Y_DYUY, kx); }, z, ex,
+                  tw, q, scale);
+      split();
+      mom3(2, f1);
+      mom3(5, f2);
+      // (du3/dx3, 0)
+      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZUZ, kx); x2 = zero; }, z, ex, tw, q, scale);
+      split();
+      mom3(8, f1);
+    }
+  }
+
+  if (MODE == XMODE_STATS || a.want_umax) {
+    for (int o = 16; o > 0; o >>= 1) {
+      const double other = __shfl_xor_sync(0xffffffffu, umax, o);
+      umax = other > umax || other != other ? other : umax;
+    }
+    if (lane == 0) atomicMax(&a.ctrl->umax_bits, (unsigned long long)__double_as_longlong(umax));
+  }
+  if constexpr (MODE == XMODE_STATS) {
+    __syncwarp();
+    const long long gw = (long long)blockIdx.x * 4 + wid;
+    for (int i = lane; i < NQ; i += 32) a.partials[gw * NQ + i] = accw[i];
+  }
+}
+
+}  // namespace psc
