@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed FP64 companion steps (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=24)
     return ap.parse_args()
 
 
@@ -148,6 +151,78 @@ def oracle_steps_per_s(nsteps: int = 2, N: int = ORACLE_SAMPLE_N):
 def oracle_scale(N_from: int, N_to: int) -> float:
     """Work ratio of one step at N_to vs N_from: N^3 log2 N."""
     return (N_to ** 3 * math.log2(N_to)) / (N_from ** 3 * math.log2(N_from))
+
+
+def ensemble_requests(seed: int = 4):
+    """64 boxes at 64^3 + 16 at 96^3 + 4 at 128^3, seeds 1000+i, k_max eta ~ U[1,2],
+    Sc from {0.7, 1, 2}, 200-1000 steps each, all present at t = 0."""
+    import numpy as np
+    from paper_2012_04838_gb300.serve import Request, nu_for_resolution
+    rng = np.random.default_rng(seed)
+    sizes = [64] * 64 + [96] * 16 + [128] * 4
+    out = []
+    for i, N in enumerate(sizes):
+        out.append(Request(rid=i, arrival=0.0, N=N, steps=int(rng.integers(200, 1001)),
+                           nu=nu_for_resolution(N, float(rng.uniform(1.0, 2.0))),
+                           Sc=float(rng.choice([0.7, 1.0, 2.0])), seed=1000 + i))
+    return out
+
+
+def run_ensemble(dev):
+    """The batched ensemble run to completion: every RK4 step of all active boxes is
+    one replay of a captured CUDA graph (rebuilt as boxes finish)."""
+    import torch
+    import paper_2012_04838_gb300 as psc
+    from paper_2012_04838_gb300.serve import Server, make_params
+    reqs = ensemble_requests()
+    res, summ = Server(budget_bytes=150e9, chunk=10 ** 9, device=dev).run(reqs)
+    out = {"metric": "ensemble sims/hr", "value": summ["sims_per_hour"], "unit": "sims/hr",
+           "boxes": len(reqs), "total_steps": sum(r.steps for r in reqs), "wall_s": summ["wall_s"],
+           "grid_point_stages_per_s": summ["grid_point_stages_per_s"],
+           "graph_builds": summ["graph_builds"], "precision": "fp32_mixed",
+           "config": "64x64^3 + 16x96^3 + 4x128^3, k_max eta in [1,2], Sc in {0.7,1,2}, "
+                     "200-1000 steps, CFL 0.5, one graph replay per ensemble step"}
+    # plain FP64 single-run path on the same GPU: each box alone, no batching;
+    # per-step time of one box per size x every box's step count
+    per_step = {}
+    for N in (64, 96, 128):
+        r = next(q for q in reqs if q.N == N)
+        p = make_params(r)
+        p.precision = psc.FP64
+        s = psc.Simulation(p, device=dev)
+        s.init_field()
+        s.step(2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(20)
+        torch.cuda.synchronize()
+        per_step[N] = (time.perf_counter() - t0) / 20
+        s.close()
+    est = sum(per_step[r.N] * r.steps for r in reqs)
+    out["fp64_single_run"] = {"sims_per_hour_est": 3600.0 * len(reqs) / est, "wall_s_est": est,
+                              "s_per_step": per_step,
+                              "how": "each box alone in FP64 via psc_step, 20 timed steps per size, "
+                                     "scaled by every box's step count"}
+    out["speedup_vs_fp64_single_run"] = out["value"] / out["fp64_single_run"]["sims_per_hour_est"]
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serve(dev, n):
+    """Poisson arrivals (4/s), N from {64,96,128,192,256}, 100-2000 steps, admitted
+    under a 150 GB budget, stepped together, records every 50 steps."""
+    import torch
+    from paper_2012_04838_gb300.serve import Server, poisson_requests
+    reqs = poisson_requests(n, rate=4.0, seed=5)
+    res, summ = Server(budget_bytes=150e9, chunk=50, device=dev).run(reqs)
+    torch.cuda.empty_cache()
+    return {"requests": summ["requests"], "p50_latency_s": summ["p50_latency_s"],
+            "p99_latency_s": summ["p99_latency_s"], "wall_s": summ["wall_s"],
+            "grid_point_stages_per_s": summ["grid_point_stages_per_s"],
+            "sims_per_hour": summ["sims_per_hour"], "peak_active": summ["peak_active"],
+            "peak_workspace_GB": summ["peak_bytes"] / 1e9, "graph_builds": summ["graph_builds"],
+            "config": f"{n} requests, Poisson 4/s, N in {{64,96,128,192,256}}, 100-2000 steps, "
+                      "k_max eta in [1,2], Sc in {0.7,1,2}, 150 GB budget, FP32-mixed"}
 
 
 # ---------------------------------------------------------------- reference arm
@@ -354,6 +429,11 @@ def main():
             torch.cuda.empty_cache()
         except Exception as e:  # report, do not hide
             out["fp64"] = {"error": str(e)[:200]}
+
+    if not a.no_ensemble:
+        out["ensemble"] = run_ensemble(dev)
+    if not a.no_serve:
+        out["serve"] = run_serve(dev, a.serve_requests)
 
     if rank == 0 and not a.no_cpu_baseline:
         sps, el = oracle_steps_per_s(2)

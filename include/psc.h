@@ -143,6 +143,24 @@ psc_status psc_rhs(psc_sim* s, const void* in, void* out);
 /* Time, step counter and current dt (host values; synchronises). */
 psc_status psc_time(psc_sim* s, double* t, int64_t* step, double* dt);
 
+/* Ensembles (boxes of any mix of N and precision stepped together).
+ *
+ * psc_batch_create() captures one RK4 step of every member into a single CUDA
+ * graph, each member on its own stream as a parallel branch forked from and
+ * joined back into `stream`; psc_batch_step() replays that graph, so an
+ * ensemble step costs one graph launch and small boxes run concurrently.
+ * Each member advances exactly as psc_step() would advance it (the step counter
+ * and the CFL decision live on the device).  Members need non-NULL streams;
+ * members that share a stream become consecutive steps of one branch (correct,
+ * but not concurrent).  `stream` must be non-NULL.  Members stay usable on their own,
+ * but their own calls and batch steps must not overlap in time: synchronise
+ * `stream` before touching a member directly, and the members' streams before
+ * the next batch step.  Profiling is suspended while the graph is captured. */
+typedef struct psc_batch psc_batch;
+psc_status psc_batch_create(psc_sim* const* sims, int32_t n, void* stream, psc_batch** out);
+psc_status psc_batch_step(psc_batch* b, int32_t nsteps); /* asynchronous on `stream` */
+psc_status psc_batch_destroy(psc_batch* b);
+
 /* Kernel classes for profiling. */
 typedef enum {
   PSC_K_FORCING = 0,  /* band energy and forcing amplitude                   */

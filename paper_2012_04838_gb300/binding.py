@@ -68,6 +68,9 @@ EXPORTS = [
     ("psc_set_state", ct.c_int, [_VP, _VP, _SZ]),
     ("psc_rhs", ct.c_int, [_VP, _VP, _VP]),
     ("psc_time", ct.c_int, [_VP, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.POINTER(ct.c_double)]),
+    ("psc_batch_create", ct.c_int, [ct.POINTER(_VP), ct.c_int32, _VP, ct.POINTER(_VP)]),
+    ("psc_batch_step", ct.c_int, [_VP, ct.c_int32]),
+    ("psc_batch_destroy", ct.c_int, [_VP]),
     ("psc_profile_enable", ct.c_int, [_VP, ct.c_int32]),
     ("psc_profile_read", ct.c_int, [_VP, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.c_int32]),
     ("psc_launch_count", ct.c_int, [_VP, ct.POINTER(ct.c_int64)]),
@@ -265,3 +268,44 @@ class Simulation:
         n = ct.c_int64()
         _check(self.lib, self.lib.psc_time(self._h, ct.byref(t), ct.byref(n), ct.byref(dt)))
         return t.value, n.value, dt.value
+
+
+class Batch:
+    """Members stepped together through one captured CUDA graph per step.
+
+    Members on different streams (``Simulation(..., stream=torch.cuda.Stream())``)
+    run as concurrent branches; members sharing a stream run one after another.
+    The batch replays on ``stream`` (a fresh stream by default).  Synchronise the
+    batch stream before touching a member directly."""
+
+    def __init__(self, sims, stream=None):
+        import torch
+        self.lib = load()
+        self.sims = list(sims)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.sims[0].device)
+        arr = (ct.c_void_p * len(self.sims))(*[s._h.value for s in self.sims])
+        self._h = ct.c_void_p()
+        for s in self.sims:
+            s.stream.synchronize()
+        with torch.cuda.device(self.sims[0].device):
+            _check(self.lib, self.lib.psc_batch_create(arr, len(self.sims),
+                                                       ct.c_void_p(self.stream.cuda_stream),
+                                                       ct.byref(self._h)))
+
+    def step(self, n: int = 1) -> None:
+        _check(self.lib, self.lib.psc_batch_step(self._h, n))
+
+    def synchronize(self) -> None:
+        self.stream.synchronize()
+
+    def close(self) -> None:
+        if self._h:
+            self.lib.psc_batch_destroy(self._h)
+            self._h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

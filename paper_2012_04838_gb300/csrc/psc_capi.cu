@@ -418,7 +418,9 @@ void rhs_passes(psc_sim* s, const void* in, bool umax) {
   launch(s, PSC_K_YINV, 1, [&] { s->tb->yinv(a, false); });
   launch(s, PSC_K_XPASS, 1, [&] { s->tb->xpass(a, XMODE_RHS); });
   if (umax && s->p.cfl > 0.0) {
-    launch(s, PSC_K_OTHER, 1, [&] { k_cfl<<<1, 32, 0, s->st>>>(s->ctrl, s->p.cfl, 2.0 * M_PI / s->p.N); });
+    launch(s, PSC_K_OTHER, 1, [&] {
+      k_cfl<<<1, 32, 0, s->st>>>(s->ctrl, s->p.cfl, 2.0 * M_PI / s->p.N, s->p.record_every);
+    });
     launch_iftab<T>(s);
   }
   launch(s, PSC_K_YFWD, 1, [&] { s->tb->yfwd(a); });
@@ -430,7 +432,9 @@ psc_status do_step(psc_sim* s, int nsteps) {
   unsigned char* U = s->ws + s->L.U;
   unsigned char* V = s->ws + s->L.V;
   for (int n = 0; n < nsteps; ++n) {
-    const bool reset_dt = s->p.cfl > 0.0 && (s->step % s->p.record_every) == 0;
+    // with a CFL target every step measures max |u| at stage 1 and the device
+    // decides whether this is a reset step, so all steps enqueue the same work
+    const bool reset_dt = s->p.cfl > 0.0;
     for (int stage = 1; stage <= 4; ++stage) {
       const void* vin = stage == 1 ? (const void*)U : (const void*)V;
       rhs_passes<T>(s, vin, stage == 1 && reset_dt);
@@ -627,6 +631,98 @@ psc_status psc_time(psc_sim* s, double* t, int64_t* step, double* dt) {
   if (t) *t = c.t;
   if (dt) *dt = c.dt;
   if (step) *step = s->step;
+  return PSC_OK;
+}
+
+}  // extern "C"
+
+struct psc_batch {
+  std::vector<psc_sim*> sims;
+  std::vector<int64_t> launches_per_step;
+  cudaStream_t st = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaEvent_t> events;
+};
+
+static void batch_free(psc_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto e : b->events) cudaEventDestroy(e);
+  delete b;
+}
+
+extern "C" {
+
+psc_status psc_batch_create(psc_sim* const* sims, int32_t n, void* stream, psc_batch** out) {
+  if (!sims || n < 1 || !out) return fail(PSC_EINVAL, "psc_batch_create: need n >= 1 members and an output handle");
+  if (!stream) return fail(PSC_EINVAL, "psc_batch_create: the batch stream must be non-NULL");
+  for (int i = 0; i < n; ++i) {
+    if (!sims[i] || !sims[i]->st) return fail(PSC_EINVAL, "psc_batch_create: members need non-NULL streams");
+    for (int j = 0; j < i; ++j)
+      if (sims[j] == sims[i]) return fail(PSC_EINVAL, "psc_batch_create: members must be distinct");
+  }
+  psc_batch* b = new (std::nothrow) psc_batch();
+  if (!b) return fail(PSC_EINVAL, "host allocation failed");
+  b->st = (cudaStream_t)stream;
+  b->sims.assign(sims, sims + n);
+  // fork/join events (one fork, one join per member)
+  b->events.resize(n + 1, nullptr);
+  for (auto& e : b->events) {
+    cudaError_t ce = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    if (ce != cudaSuccess) { batch_free(b); return cuda_fail(ce, "psc_batch_create"); }
+  }
+  std::vector<bool> prof(n);
+  std::vector<int64_t> step0(n), launch0(n);
+  for (int i = 0; i < n; ++i) {
+    prof[i] = sims[i]->profiling;
+    sims[i]->profiling = false;
+    step0[i] = sims[i]->step;
+    launch0[i] = sims[i]->launches;
+  }
+  cudaError_t e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeRelaxed);
+  psc_status st = PSC_OK;
+  if (e == cudaSuccess) e = cudaEventRecord(b->events[0], b->st);
+  for (int i = 0; i < n && e == cudaSuccess && st == PSC_OK; ++i) {
+    psc_sim* m = sims[i];
+    if (m->st != b->st) e = cudaStreamWaitEvent(m->st, b->events[0], 0);
+    if (e != cudaSuccess) break;
+    st = m->fp64 ? do_step<double>(m, 1) : do_step<float>(m, 1);
+    if (st == PSC_OK && m->st != b->st) {
+      e = cudaEventRecord(b->events[i + 1], m->st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->events[i + 1], 0);
+    }
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(b->st, &g);
+  for (int i = 0; i < n; ++i) {
+    sims[i]->profiling = prof[i];
+    b->launches_per_step.push_back(sims[i]->launches - launch0[i]);
+    sims[i]->step = step0[i];
+    sims[i]->launches = launch0[i];
+  }
+  if (st != PSC_OK) { if (g) cudaGraphDestroy(g); batch_free(b); return st; }
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) { b->graph = g; e = cudaGraphInstantiate(&b->exec, g, 0); }
+  else if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) { batch_free(b); return cuda_fail(e, "psc_batch_create: graph capture"); }
+  *out = b;
+  return PSC_OK;
+}
+
+psc_status psc_batch_step(psc_batch* b, int32_t nsteps) {
+  if (!b) return fail(PSC_EINVAL, "null batch");
+  if (nsteps < 0) return fail(PSC_EINVAL, "nsteps must be >= 0");
+  for (int k = 0; k < nsteps; ++k) PSC_CUDA(cudaGraphLaunch(b->exec, b->st));
+  for (size_t i = 0; i < b->sims.size(); ++i) {
+    b->sims[i]->step += nsteps;
+    b->sims[i]->launches += nsteps * b->launches_per_step[i];
+  }
+  return PSC_OK;
+}
+
+psc_status psc_batch_destroy(psc_batch* b) {
+  if (b) batch_free(b);
   return PSC_OK;
 }
 

@@ -46,6 +46,7 @@ struct Ctrl {
   int err;                        // bit 0: index check failed; bit 1: non-finite velocity
   int pad;
   double moments[NQ];
+  long long step;                 // RK4 steps taken (advanced by the last stage of each step)
 };
 
 // Streams of the intermediate buffers (indices into zb / yb).

@@ -43,7 +43,10 @@ __global__ void __launch_bounds__(256) k_combine(CombineArgs c) {
   const Dims& d = c.d;
   const long long S = d.S;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (STAGE == 4 && i == 0) c.ctrl->t += c.ctrl->dt;
+  if (STAGE == 4 && i == 0) {
+    c.ctrl->t += c.ctrl->dt;
+    c.ctrl->step += 1;
+  }
   if (i >= S) return;
   int kx, ky, kz;
   mode_of(d, i, kx, ky, kz);
@@ -169,10 +172,13 @@ __global__ void k_iftab(int K, const Ctrl* ctrl, double nu, double D, T* eu, T* 
 }
 
 #ifndef PSC_SHELLS_ONLY
-// dt = cfl dx / max(|u1|+|u2|+|u3|)  (Eq. 10); a non-finite maximum raises
-// the instability flag and leaves dt unchanged.
-__global__ void k_cfl(Ctrl* c, double cfl, double dx) {
+// dt = cfl dx / max(|u1|+|u2|+|u3|)  (Eq. 10) on every record_every-th step
+// (the step count lives on the device, so the launch sequence of a step never
+// changes and can be captured in a CUDA graph); a non-finite maximum raises the
+// instability flag and leaves dt unchanged.
+__global__ void k_cfl(Ctrl* c, double cfl, double dx, int record_every) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (c->step % record_every != 0) return;
   const double m = __longlong_as_double((long long)c->umax_bits);
   if (!(m <= 1.7976931348623157e308)) { c->err |= 2; return; }
   if (m > 0.0) c->dt = cfl * dx / m;
