@@ -44,15 +44,35 @@ template <typename T, int N, int W> struct StridedSmem {
   static constexpr int CPB = 128 / (int)sizeof(C);
   static constexpr int PAD = (W >= CPB) ? 0 : ((((W - R2 * W) % CPB) + CPB) % CPB);
   static constexpr int ROW = R2 * W + PAD;
-  static constexpr size_t BYTES = (size_t)R1 * ROW * sizeof(C);
+  static constexpr size_t EXCH_BYTES = (size_t)R1 * ROW * sizeof(C);
+  // step-1 twiddles wN^(n2 k1) for this CTA's threads, stored [j][k1][t]
+  // (n2 = t + j TPL) so a warp reads consecutive or identical entries
+  static constexpr size_t BYTES = EXCH_BYTES + (size_t)N * sizeof(C);
 };
+
+// Fill the shared twiddle table of the strided passes (call before the first
+// transform; ends with a barrier).
+template <typename T, int N, int W>
+__device__ __forceinline__ typename CT<T>::type* strided_twiddles(unsigned char* smraw,
+                                                                  const typename CT<T>::type* __restrict__ tw) {
+  using C = typename CT<T>::type;
+  using PL = PlanD<N>;
+  C* t = reinterpret_cast<C*>(smraw + StridedSmem<T, N, W>::EXCH_BYTES);
+  const int nthr = blockDim.x * blockDim.y, me = threadIdx.y * blockDim.x + threadIdx.x;
+  for (int i = me; i < N; i += nthr) {
+    const int tt = i % PL::TPL, k1 = (i / PL::TPL) % PL::R1, j = i / (PL::TPL * PL::R1);
+    t[i] = tw[(tt + j * PL::TPL) * k1];
+  }
+  __syncthreads();
+  return t;
+}
 
 // One length-N DFT per column, direction DIR (-1 forward, +1 inverse).
 // ld(p) returns the element at line position p; st(k, v) stores output k.
 template <typename T, int N, int W, int DIR, class LD, class ST>
 __device__ __forceinline__ void strided_fft(const LD& ld, const ST& st,
                                             typename CT<T>::type* sm,
-                                            const typename CT<T>::type* __restrict__ tw,
+                                            const typename CT<T>::type* twsm,
                                             int t, int w) {
   using C = typename CT<T>::type;
   using PL = PlanD<N>;
@@ -69,7 +89,7 @@ __device__ __forceinline__ void strided_fft(const LD& ld, const ST& st,
     for (int k1 = 0; k1 < R1; ++k1) {
       C v = a[k1];
       if (k1 > 0) {
-        const C wv = tw[n2 * k1];
+        const C wv = twsm[(j * R1 + k1) * TPL + t];  // wN^(n2 k1)
         v = (DIR < 0) ? cmul(v, wv) : cmulc(v, wv);
       }
       sm[k1 * SM::ROW + n2 * W + w] = v;
@@ -114,7 +134,7 @@ k_zinv(PassArgs a) {
   const bool act = ix < M;
   const C* __restrict__ in = static_cast<const C*>(a.in);
   C* __restrict__ zb = static_cast<C*>(a.zb);
-  const C* __restrict__ tw = static_cast<const C*>(a.tw);
+  const C* tw = strided_twiddles<T, N, W>(smraw, static_cast<const C*>(a.tw));
   const long long S = (long long)P * P * M, zs = (long long)N * P * M;
   const C zero = mk(T(0), T(0));
   // (input field, multiply by i kz, output stream)
@@ -165,7 +185,7 @@ k_yinv(PassArgs a) {
   const bool act = ix < M;
   const C* __restrict__ zb = static_cast<const C*>(a.zb);
   C* __restrict__ yb = static_cast<C*>(a.yb);
-  const C* __restrict__ tw = static_cast<const C*>(a.tw);
+  const C* tw = strided_twiddles<T, N, W>(smraw, static_cast<const C*>(a.tw));
   const long long zs = (long long)N * P * M, ys = (long long)N * N * M;
   const C zero = mk(T(0), T(0));
   // (kind, s1, s2, out): kind 0 = s1, 1 = i ky s1, 2 = i ky s1 - s2
@@ -222,7 +242,7 @@ k_yfwd(PassArgs a) {
   const bool act = ix < M;
   const C* __restrict__ xb = static_cast<const C*>(a.xb);
   C* __restrict__ yf = static_cast<C*>(a.yf);
-  const C* __restrict__ tw = static_cast<const C*>(a.tw);
+  const C* tw = strided_twiddles<T, N, W>(smraw, static_cast<const C*>(a.tw));
   const long long zs = (long long)N * P * M, ys = (long long)N * N * M;
   const C zero = mk(T(0), T(0));
 #pragma unroll 1
@@ -257,7 +277,7 @@ k_zfwd(PassArgs a) {
   const bool act = ix < M;
   const C* __restrict__ yf = static_cast<const C*>(a.yf);
   C* __restrict__ rb = static_cast<C*>(a.rb);
-  const C* __restrict__ tw = static_cast<const C*>(a.tw);
+  const C* tw = strided_twiddles<T, N, W>(smraw, static_cast<const C*>(a.tw));
   const long long S = (long long)P * P * M, zs = (long long)N * P * M;
   const C zero = mk(T(0), T(0));
 #pragma unroll 1
@@ -709,16 +729,16 @@ template <typename T, int N> struct Passes {
         prep(k_xpass2<T, N, XMODE_RHS>, sm2);
         k_xpass2<T, N, XMODE_RHS><<<xgrid(), 128, sm2, a.st>>>(a);
       }
-      return;
-    }
-    const size_t sm = XCfg<T, N>::SMEM;
-    dim3 block(32 * XCfg<T, N>::WARPS);
-    if (mode == XMODE_STATS) {
-      prep(k_xpass<T, N, XMODE_STATS>, sm);
-      k_xpass<T, N, XMODE_STATS><<<xgrid(), block, sm, a.st>>>(a);
     } else {
-      prep(k_xpass<T, N, XMODE_RHS>, sm);
-      k_xpass<T, N, XMODE_RHS><<<xgrid(), block, sm, a.st>>>(a);
+      const size_t sm = XCfg<T, N>::SMEM;
+      dim3 block(32 * XCfg<T, N>::WARPS);
+      if (mode == XMODE_STATS) {
+        prep(k_xpass<T, N, XMODE_STATS>, sm);
+        k_xpass<T, N, XMODE_STATS><<<xgrid(), block, sm, a.st>>>(a);
+      } else {
+        prep(k_xpass<T, N, XMODE_RHS>, sm);
+        k_xpass<T, N, XMODE_RHS><<<xgrid(), block, sm, a.st>>>(a);
+      }
     }
   }
   static void yfwd(const PassArgs& a) {

@@ -30,7 +30,13 @@ template <typename T, int N> struct X2Cfg {
   static constexpr int EXCH = 16 * ROW > N ? 16 * ROW : N;
   static constexpr size_t LINE_BYTES = (EXCH * sizeof(C) + 15) / 16 * 16;
   static constexpr size_t ACC_BYTES = 4 * NQ * sizeof(double);
-  static constexpr size_t SMEM = LINE_BYTES * ROWS + ACC_BYTES;
+  // per-role twiddle tables (every row of the CTA uses the same thread roles):
+  //   T1[a][tid]  = wN^(a tid)             (inverse step after the first DFT-16)
+  //   T3[k1][tid] = wN^(ra (rk0 + G k1))   (forward step before the exchange)
+  //   T2[b][k0]   = wN^(16 b k0)           (between the lane DFT and the DFT-16 over b)
+  // laid out so the 32 lanes of a warp read consecutive entries
+  static constexpr size_t TW_BYTES = (size_t)(2 * 16 * TH + 16 * G) * sizeof(C);
+  static constexpr size_t SMEM = LINE_BYTES * ROWS + ACC_BYTES + TW_BYTES;
   static constexpr int K = (N - 1) / 3;
   static_assert(N == 512 || N == 1024, "X2 layout covers N = 512 and 1024");
 };
@@ -81,12 +87,15 @@ __device__ __forceinline__ void lane_dft(typename CT<T>::type (&v)[16], int r) {
   }
 }
 
-struct X2Roles {
+template <typename C> struct X2Roles {
   int tid;  // thread within the row: inverse input / forward output column j
   int ra;   // a of the (a, r) role
   int rr;   // r of the (a, r) role (lane within the G-group)
   int rk0;  // k0 held by lane rr between the lane DFT and the DFT-16 over b
   int bar;  // named barrier of this row
+  const C* t1;  // shared twiddle tables, see X2Cfg
+  const C* t2;
+  const C* t3;
 };
 
 // Inverse transform of a Hermitian-packed half spectrum (two real fields):
@@ -95,8 +104,7 @@ struct X2Roles {
 // z[b] = scale * IDFT(Z) at n = ra + 16 b + 256 rr.
 template <typename T, int N, class SPEC>
 __device__ __forceinline__ void x2inv(const SPEC& spec, typename CT<T>::type (&z)[16],
-                                      typename CT<T>::type* ex,
-                                      const typename CT<T>::type* __restrict__ tw, const X2Roles& q,
+                                      typename CT<T>::type* ex, const X2Roles<typename CT<T>::type>& q,
                                       T scale) {
   using C = typename CT<T>::type;
   using XC = X2Cfg<T, N>;
@@ -121,7 +129,7 @@ __device__ __forceinline__ void x2inv(const SPEC& spec, typename CT<T>::type (&z
 #pragma unroll
   for (int a = 0; a < 16; ++a) {
     C w = v[a];
-    if (a > 0) w = cmulc(w, tw[a * q.tid]);  // wN^(-a j)
+    if (a > 0) w = cmulc(w, q.t1[a * TH + q.tid]);  // wN^(-a j)
     ex[a * ROW + q.tid] = w;
   }
   row_sync<TH>(q.bar);
@@ -131,7 +139,7 @@ __device__ __forceinline__ void x2inv(const SPEC& spec, typename CT<T>::type (&z
   Dft<16, +1>::template run<T, C>(z);  // over k1 -> b
   if (q.rk0 > 0) {
 #pragma unroll
-    for (int b = 1; b < 16; ++b) z[b] = cmulc(z[b], tw[16 * b * q.rk0]);  // wN^(-16 b k0)
+    for (int b = 1; b < 16; ++b) z[b] = cmulc(z[b], q.t2[b * G + q.rk0]);  // wN^(-16 b k0)
   }
   lane_dft<T, G, +1>(z, q.rr);  // over k0 -> c
 #pragma unroll
@@ -142,22 +150,21 @@ __device__ __forceinline__ void x2inv(const SPEC& spec, typename CT<T>::type (&z
 // x2inv leaves them in; out(kx, X1, X2) receives both half spectra for kx <= K.
 template <typename T, int N, class OUT>
 __device__ __forceinline__ void x2fwd(typename CT<T>::type (&z)[16], const OUT& out,
-                                      typename CT<T>::type* ex,
-                                      const typename CT<T>::type* __restrict__ tw, const X2Roles& q) {
+                                      typename CT<T>::type* ex, const X2Roles<typename CT<T>::type>& q) {
   using C = typename CT<T>::type;
   using XC = X2Cfg<T, N>;
   constexpr int TH = XC::TH, G = XC::G, ROW = XC::ROW, K = XC::K;
   lane_dft<T, G, -1>(z, q.rr);  // over c -> k0
   if (q.rk0 > 0) {
 #pragma unroll
-    for (int b = 1; b < 16; ++b) z[b] = cmul(z[b], tw[16 * b * q.rk0]);  // wN^(16 b k0)
+    for (int b = 1; b < 16; ++b) z[b] = cmul(z[b], q.t2[b * G + q.rk0]);  // wN^(16 b k0)
   }
   Dft<16, -1>::template run<T, C>(z);  // over b -> k1
 #pragma unroll
   for (int k1 = 0; k1 < 16; ++k1) {
     const int j = q.rk0 + G * k1;
     C w = z[k1];
-    if (q.ra > 0 && j > 0) w = cmul(w, tw[q.ra * j]);  // wN^(a (k0 + G k1))
+    if (q.ra > 0 && j > 0) w = cmul(w, q.t3[k1 * TH + q.tid]);  // wN^(a (k0 + G k1))
     ex[q.ra * ROW + j] = w;
   }
   row_sync<TH>(q.bar);
@@ -193,7 +200,7 @@ __global__ void __launch_bounds__(128, 3) k_xpass2(PassArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int lid = threadIdx.x / TH;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  X2Roles q;
+  X2Roles<C> q;
   q.tid = threadIdx.x % TH;
   q.ra = q.tid / G;
   q.rr = q.tid % G;
@@ -204,6 +211,22 @@ __global__ void __launch_bounds__(128, 3) k_xpass2(PassArgs a) {
   const C* __restrict__ yb = static_cast<const C*>(a.yb);
   C* __restrict__ xb = static_cast<C*>(a.xb);
   const C* __restrict__ tw = static_cast<const C*>(a.tw);
+  {
+    C* t1 = reinterpret_cast<C*>(smraw + XC::LINE_BYTES * ROWS + XC::ACC_BYTES);
+    C* t3 = t1 + 16 * TH;
+    C* t2 = t3 + 16 * TH;
+    for (int i = threadIdx.x; i < 16 * TH; i += blockDim.x) {
+      const int e = i / TH, tid = i % TH;  // e = a for T1, k1 for T3
+      const int ra = tid / G, rk0 = bitrev_lane<G>(tid % G);
+      t1[i] = tw[e * tid];
+      t3[i] = tw[ra * (rk0 + G * e)];
+    }
+    for (int i = threadIdx.x; i < 16 * G; i += blockDim.x) t2[i] = tw[16 * (i / G) * (i % G)];
+    q.t1 = t1;
+    q.t2 = t2;
+    q.t3 = t3;
+    __syncthreads();
+  }
   const long long ys = (long long)N * N * M;
   const long long nlines = (long long)N * N;
   const T scale = T(1.0 / ((double)N * N * N));
@@ -226,11 +249,11 @@ __global__ void __launch_bounds__(128, 3) k_xpass2(PassArgs a) {
     if constexpr (MODE == XMODE_RHS) {
       T u1[16], u2[16], u3[16], A1[16], A2[16];
       // (u1, u2)
-      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UY, kx); }, z, ex, tw, q, scale);
+      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UY, kx); }, z, ex, q, scale);
 #pragma unroll
       for (int b = 0; b < 16; ++b) { u1[b] = z[b].x; u2[b] = z[b].y; }
       // (u3, omega1)
-      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UZ, kx); x2 = Y(Y_WX, kx); }, z, ex, tw, q, scale);
+      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UZ, kx); x2 = Y(Y_WX, kx); }, z, ex, q, scale);
 #pragma unroll
       for (int b = 0; b < 16; ++b) {
         u3[b] = z[b].x;
@@ -247,7 +270,7 @@ __global__ void __launch_bounds__(128, 3) k_xpass2(PassArgs a) {
             x1 = csub(Y(Y_DZUX, kx), mul_ik(Y(Y_UZ, kx), T(kx)));
             x2 = csub(mul_ik(Y(Y_UY, kx), T(kx)), Y(Y_DYUX, kx));
           },
-          z, ex, tw, q, scale);
+          z, ex, q, scale);
 #pragma unroll
       for (int b = 0; b < 16; ++b) {
         const T w2 = z[b].x, w3 = z[b].y;
@@ -259,14 +282,14 @@ __global__ void __launch_bounds__(128, 3) k_xpass2(PassArgs a) {
                     const long long i0 = line * M + kx;
                     if (PSC_OK_INDEX(i0 + ys, 4 * ys, a.ctrl)) { xb[i0] = X1; xb[i0 + ys] = X2; }
                   },
-                  ex, tw, q);
+                  ex, q);
       // (dphi/dx1, dphi/dx2)
       x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_PHI, kx), T(kx)); x2 = Y(Y_DYPHI, kx); },
-                  z, ex, tw, q, scale);
+                  z, ex, q, scale);
 #pragma unroll
       for (int b = 0; b < 16; ++b) A1[b] = u1[b] * z[b].x + u2[b] * z[b].y;
       // (dphi/dx3, 0)
-      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZPHI, kx); x2 = zero; }, z, ex, tw, q, scale);
+      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZPHI, kx); x2 = zero; }, z, ex, q, scale);
 #pragma unroll
       for (int b = 0; b < 16; ++b) z[b] = mk(A2[b], A1[b] + u3[b] * z[b].x);  // (NL3, u.grad phi)
       x2fwd<T, N>(z,
@@ -274,7 +297,7 @@ __global__ void __launch_bounds__(128, 3) k_xpass2(PassArgs a) {
                     const long long i0 = 2 * ys + line * M + kx;
                     if (PSC_OK_INDEX(i0 + ys, 4 * ys, a.ctrl)) { xb[i0] = X1; xb[i0 + ys] = X2; }
                   },
-                  ex, tw, q);
+                  ex, q);
     } else {
       // statistics (Eqs. 11-13): per pair, FP32/FP64 partial sums of the thread's
       // 16 points, reduced over the warp in FP64 into the warp's accumulators
@@ -295,7 +318,7 @@ __global__ void __launch_bounds__(128, 3) k_xpass2(PassArgs a) {
         for (int b = 0; b < 16; ++b) { f1[b] = z[b].x; f2[b] = z[b].y; }
       };
       // (u1, u3)
-      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UZ, kx); }, z, ex, tw, q, scale);
+      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UZ, kx); }, z, ex, q, scale);
       split();
       {
         T s = T(0);
@@ -304,7 +327,7 @@ __global__ void __launch_bounds__(128, 3) k_xpass2(PassArgs a) {
         put(0, s);
       }
       // (u2, phi)
-      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UY, kx); x2 = Y(Y_PHI, kx); }, z, ex, tw, q, scale);
+      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UY, kx); x2 = Y(Y_PHI, kx); }, z, ex, q, scale);
       split();
       {
         T s0 = T(0), s1 = T(0), s2 = T(0);
@@ -319,7 +342,7 @@ __global__ void __launch_bounds__(128, 3) k_xpass2(PassArgs a) {
       // (omega1, omega2)
       x2inv<T, N>(
           [&](int kx, C& x1, C& x2) { x1 = Y(Y_WX, kx); x2 = csub(Y(Y_DZUX, kx), mul_ik(Y(Y_UZ, kx), T(kx))); },
-          z, ex, tw, q, scale);
+          z, ex, q, scale);
       split();
       {
         T s = T(0);
@@ -333,7 +356,7 @@ __global__ void __launch_bounds__(128, 3) k_xpass2(PassArgs a) {
             x1 = csub(mul_ik(Y(Y_UY, kx), T(kx)), Y(Y_DYUX, kx));
             x2 = mul_ik(Y(Y_PHI, kx), T(kx));
           },
-          z, ex, tw, q, scale);
+          z, ex, q, scale);
       split();
       {
         T s = T(0);
@@ -343,18 +366,18 @@ __global__ void __launch_bounds__(128, 3) k_xpass2(PassArgs a) {
         mom3(11, f2);
       }
       // (dphi/dx2, dphi/dx3)
-      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DYPHI, kx); x2 = Y(Y_DZPHI, kx); }, z, ex, tw, q, scale);
+      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DYPHI, kx); x2 = Y(Y_DZPHI, kx); }, z, ex, q, scale);
       split();
       mom3(14, f1);
       mom3(17, f2);
       // (du1/dx1, du2/dx2)
       x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_UX, kx), T(kx)); x2 = Y(Y_DYUY, kx); }, z, ex,
-                  tw, q, scale);
+                  q, scale);
       split();
       mom3(2, f1);
       mom3(5, f2);
       // (du3/dx3, 0)
-      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZUZ, kx); x2 = zero; }, z, ex, tw, q, scale);
+      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZUZ, kx); x2 = zero; }, z, ex, q, scale);
       split();
       mom3(8, f1);
     }
