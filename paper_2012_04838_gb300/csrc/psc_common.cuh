@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "psc_internal.h"
 #include "codelets.cuh"
 
@@ -68,6 +70,22 @@ template <int N> struct PlanD : Plan<N> {
   static_assert(R1 % TPL == 0 && R2 % TPL == 0, "TPL must divide both radices");
   static_assert(32 % TPL == 0, "a line's threads must sit inside one warp");
 };
+
+// f(std::integral_constant<int, I>) for I = B .. E-1, each index a compile-time constant
+template <int B, int E, class F> __device__ __forceinline__ void static_for(const F& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
+
+// Positions j + TH m (j < TH) of a length-N line split into 16 slots of TH:
+// 1 if every such position is retained (|k| <= K), 0 if none is, 2 if mixed.
+__host__ __device__ constexpr int band_of(int N, int TH, int m) {
+  return (TH * m + TH - 1 <= (N - 1) / 3 || TH * m >= N - (N - 1) / 3) ? 1
+         : (TH * m > (N - 1) / 3 && TH * m + TH - 1 < N - (N - 1) / 3) ? 0
+                                                                      : 2;
+}
 
 // Optional index checks (build with -DPSC_CHECKED=1): an out-of-range global
 // index is not accessed; bit 0 of Ctrl::err is raised instead.

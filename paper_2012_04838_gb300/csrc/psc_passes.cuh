@@ -28,8 +28,12 @@ namespace psc {
 // W-wide contiguous run of complex values.
 // ---------------------------------------------------------------------------
 
-template <typename T, int N> struct StridedCfg {
-  static constexpr int W = (sizeof(T) == 4) ? ((N >= 512) ? 8 : 16) : 8;
+// Column tile width per pass (measured on GB300 at 512^3 and 1024^3 in FP32:
+// 128-byte runs pay off for the z passes, 64-byte runs with two CTAs per SM
+// for the y passes).
+enum { PASS_Z = 0, PASS_Y = 1 };
+template <typename T, int N, int AXIS = PASS_Z> struct StridedCfg {
+  static constexpr int W = (sizeof(T) == 4) ? ((N >= 512 && AXIS == PASS_Y) ? 8 : 16) : 8;
   static constexpr int THREADS = W * PlanD<N>::TPL;
   // FP32: cap registers at 128 per thread so at least 512 threads fit on an SM;
   // FP64 is bound by the FP64 pipe, so it keeps its values in registers instead
@@ -122,10 +126,10 @@ template <int N> __device__ __forceinline__ bool k_of_pos(int p, int& k) {
 // runtime loop over its stream table), so the instruction footprint stays that
 // of a single two-step FFT however many streams the pass carries.
 template <typename T, int N, bool STATS>
-__global__ void __launch_bounds__(StridedCfg<T, N>::THREADS, StridedCfg<T, N>::MINB)
+__global__ void __launch_bounds__(StridedCfg<T, N, PASS_Z>::THREADS, StridedCfg<T, N, PASS_Z>::MINB)
 k_zinv(PassArgs a) {
   using C = typename CT<T>::type;
-  constexpr int W = StridedCfg<T, N>::W, K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
+  constexpr int W = StridedCfg<T, N, PASS_Z>::W, K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int w = threadIdx.x, t = threadIdx.y;
@@ -173,10 +177,10 @@ k_zinv(PassArgs a) {
 }
 
 template <typename T, int N, bool STATS>
-__global__ void __launch_bounds__(StridedCfg<T, N>::THREADS, StridedCfg<T, N>::MINB)
+__global__ void __launch_bounds__(StridedCfg<T, N, PASS_Y>::THREADS, StridedCfg<T, N, PASS_Y>::MINB)
 k_yinv(PassArgs a) {
   using C = typename CT<T>::type;
-  constexpr int W = StridedCfg<T, N>::W, K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
+  constexpr int W = StridedCfg<T, N, PASS_Y>::W, K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int w = threadIdx.x, t = threadIdx.y;
@@ -230,10 +234,10 @@ k_yinv(PassArgs a) {
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(StridedCfg<T, N>::THREADS, StridedCfg<T, N>::MINB)
+__global__ void __launch_bounds__(StridedCfg<T, N, PASS_Y>::THREADS, StridedCfg<T, N, PASS_Y>::MINB)
 k_yfwd(PassArgs a) {
   using C = typename CT<T>::type;
-  constexpr int W = StridedCfg<T, N>::W, K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
+  constexpr int W = StridedCfg<T, N, PASS_Y>::W, K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int w = threadIdx.x, t = threadIdx.y;
@@ -265,10 +269,10 @@ k_yfwd(PassArgs a) {
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(StridedCfg<T, N>::THREADS, StridedCfg<T, N>::MINB)
+__global__ void __launch_bounds__(StridedCfg<T, N, PASS_Z>::THREADS, StridedCfg<T, N, PASS_Z>::MINB)
 k_zfwd(PassArgs a) {
   using C = typename CT<T>::type;
-  constexpr int W = StridedCfg<T, N>::W, K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
+  constexpr int W = StridedCfg<T, N, PASS_Z>::W, K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int w = threadIdx.x, t = threadIdx.y;
@@ -684,10 +688,10 @@ namespace psc {
 // ---------------------------------------------------------------------------
 
 template <typename T, int N> struct Passes {
-  static constexpr int W = StridedCfg<T, N>::W;
+  static constexpr int WZ = StridedCfg<T, N, PASS_Z>::W, WY = StridedCfg<T, N, PASS_Y>::W;
   static constexpr int TPL = PlanD<N>::TPL;
   static constexpr int M = PlanD<N>::M, P = PlanD<N>::P;
-  static constexpr size_t SSM = StridedSmem<T, N, W>::BYTES;
+  static constexpr size_t SSMZ = StridedSmem<T, N, WZ>::BYTES, SSMY = StridedSmem<T, N, WY>::BYTES;
 
   // rows of N = 512 and 1024 use the 16-values-per-thread layout of psc_xpass2.cuh
   static constexpr bool X2 = (N == 512 || N == 1024);
@@ -710,14 +714,14 @@ template <typename T, int N> struct Passes {
   }
 
   static void zinv(const PassArgs& a, bool stats) {
-    dim3 grid((M + W - 1) / W, P), block(W, TPL);
-    if (stats) { prep(k_zinv<T, N, true>, SSM); k_zinv<T, N, true><<<grid, block, SSM, a.st>>>(a); }
-    else { prep(k_zinv<T, N, false>, SSM); k_zinv<T, N, false><<<grid, block, SSM, a.st>>>(a); }
+    dim3 grid((M + WZ - 1) / WZ, P), block(WZ, TPL);
+    if (stats) { prep(k_zinv<T, N, true>, SSMZ); k_zinv<T, N, true><<<grid, block, SSMZ, a.st>>>(a); }
+    else { prep(k_zinv<T, N, false>, SSMZ); k_zinv<T, N, false><<<grid, block, SSMZ, a.st>>>(a); }
   }
   static void yinv(const PassArgs& a, bool stats) {
-    dim3 grid((M + W - 1) / W, N), block(W, TPL);
-    if (stats) { prep(k_yinv<T, N, true>, SSM); k_yinv<T, N, true><<<grid, block, SSM, a.st>>>(a); }
-    else { prep(k_yinv<T, N, false>, SSM); k_yinv<T, N, false><<<grid, block, SSM, a.st>>>(a); }
+    dim3 grid((M + WY - 1) / WY, N), block(WY, TPL);
+    if (stats) { prep(k_yinv<T, N, true>, SSMY); k_yinv<T, N, true><<<grid, block, SSMY, a.st>>>(a); }
+    else { prep(k_yinv<T, N, false>, SSMY); k_yinv<T, N, false><<<grid, block, SSMY, a.st>>>(a); }
   }
   static void xpass(const PassArgs& a, int mode) {
     if constexpr (X2) {
@@ -742,14 +746,14 @@ template <typename T, int N> struct Passes {
     }
   }
   static void yfwd(const PassArgs& a) {
-    dim3 grid((M + W - 1) / W, N), block(W, TPL);
-    prep(k_yfwd<T, N>, SSM);
-    k_yfwd<T, N><<<grid, block, SSM, a.st>>>(a);
+    dim3 grid((M + WY - 1) / WY, N), block(WY, TPL);
+    prep(k_yfwd<T, N>, SSMY);
+    k_yfwd<T, N><<<grid, block, SSMY, a.st>>>(a);
   }
   static void zfwd(const PassArgs& a) {
-    dim3 grid((M + W - 1) / W, P), block(W, TPL);
-    prep(k_zfwd<T, N>, SSM);
-    k_zfwd<T, N><<<grid, block, SSM, a.st>>>(a);
+    dim3 grid((M + WZ - 1) / WZ, P), block(WZ, TPL);
+    prep(k_zfwd<T, N>, SSMZ);
+    k_zfwd<T, N><<<grid, block, SSMZ, a.st>>>(a);
   }
   static const PassTable* table() {
     static const PassTable tb = {&zinv, &yinv, &xpass, &yfwd, &zfwd,

@@ -101,8 +101,9 @@ template <typename C> struct X2Roles {
 // Inverse transform of a Hermitian-packed half spectrum (two real fields):
 // Z[p] = X1[p] + i X2[p] (p <= K, imaginary parts dropped at p = 0),
 // conj(X1[N-p]) + i conj(X2[N-p]) (p >= N-K), 0 elsewhere.  On return
-// z[b] = scale * IDFT(Z) at n = ra + 16 b + 256 rr.
-template <typename T, int N, class SPEC>
+// z[b] = scale * IDFT(Z) at n = ra + 16 b + 256 rr (SCALE = false: the
+// unscaled IDFT; the caller folds 1/N^3 into its products).
+template <typename T, int N, bool SCALE = true, class SPEC>
 __device__ __forceinline__ void x2inv(const SPEC& spec, typename CT<T>::type (&z)[16],
                                       typename CT<T>::type* ex, const X2Roles<typename CT<T>::type>& q,
                                       T scale) {
@@ -110,21 +111,35 @@ __device__ __forceinline__ void x2inv(const SPEC& spec, typename CT<T>::type (&z
   using XC = X2Cfg<T, N>;
   constexpr int TH = XC::TH, G = XC::G, ROW = XC::ROW, K = XC::K;
   C v[16];
-#pragma unroll
-  for (int m = 0; m < 16; ++m) {
+  // slots whose positions all lie in the zero band load nothing; slots wholly
+  // inside [0, K] or [N-K, N) need no range test
+  static_for<0, 16>([&](auto mc) {
+    constexpr int m = decltype(mc)::value;
+    constexpr int band = band_of(N, TH, m);
+    constexpr bool low = TH * m <= K;  // slot starts in [0, K]
     const int p = q.tid + TH * m;
     C x1, x2;
-    if (p <= K) {
+    if constexpr (band == 0) {
+      v[m] = mk(T(0), T(0));
+    } else if constexpr (band == 1 && low) {
       spec(p, x1, x2);
-      if (p == 0) { x1.y = T(0); x2.y = T(0); }
+      if (m == 0 && p == 0) { x1.y = T(0); x2.y = T(0); }
       v[m] = mk(x1.x - x2.y, x1.y + x2.x);
-    } else if (p >= N - K) {
+    } else if constexpr (band == 1) {
       spec(N - p, x1, x2);
       v[m] = mk(x1.x + x2.y, x2.x - x1.y);
     } else {
-      v[m] = mk(T(0), T(0));
+      if (p <= K) {
+        spec(p, x1, x2);
+        v[m] = mk(x1.x - x2.y, x1.y + x2.x);
+      } else if (p >= N - K) {
+        spec(N - p, x1, x2);
+        v[m] = mk(x1.x + x2.y, x2.x - x1.y);
+      } else {
+        v[m] = mk(T(0), T(0));
+      }
     }
-  }
+  });
   Dft<16, +1>::template run<T, C>(v);  // over k2 -> a
 #pragma unroll
   for (int a = 0; a < 16; ++a) {
@@ -142,8 +157,10 @@ __device__ __forceinline__ void x2inv(const SPEC& spec, typename CT<T>::type (&z
     for (int b = 1; b < 16; ++b) z[b] = cmulc(z[b], q.t2[b * G + q.rk0]);  // wN^(-16 b k0)
   }
   lane_dft<T, G, +1>(z, q.rr);  // over k0 -> c
+  if constexpr (SCALE) {
 #pragma unroll
-  for (int b = 0; b < 16; ++b) z[b] = cscale(z[b], scale);
+    for (int b = 0; b < 16; ++b) z[b] = cscale(z[b], scale);
+  }
 }
 
 // Forward transform of two real fields packed as x1 + i x2 at the positions
@@ -173,8 +190,12 @@ __device__ __forceinline__ void x2fwd(typename CT<T>::type (&z)[16], const OUT& 
   for (int a = 0; a < 16; ++a) v[a] = ex[a * ROW + q.tid];
   row_sync<TH>(q.bar);
   Dft<16, -1>::template run<T, C>(v);  // over a -> k2
-#pragma unroll
-  for (int k2 = 0; k2 < 16; ++k2) ex[q.tid + TH * k2] = v[k2];  // natural order
+  // natural order; outputs that can never be retained are not stored (and so
+  // not computed)
+  static_for<0, 16>([&](auto kc) {
+    constexpr int k2 = decltype(kc)::value;
+    if constexpr (band_of(N, TH, k2) != 0) ex[q.tid + TH * k2] = v[k2];
+  });
   row_sync<TH>(q.bar);
   for (int kx = q.tid; kx <= K; kx += TH) {
     const C A = ex[kx];
@@ -247,25 +268,28 @@ __global__ void __launch_bounds__(128, 3) k_xpass2(PassArgs a) {
     };
     C z[16];
     if constexpr (MODE == XMODE_RHS) {
+      // the inverse transforms are left unscaled (N^3 times the fields); each
+      // product carries the missing 1/N^6 once
+      const T s2 = scale * scale;
       T u1[16], u2[16], u3[16], A1[16], A2[16];
       // (u1, u2)
-      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UY, kx); }, z, ex, q, scale);
+      x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UY, kx); }, z, ex, q, scale);
 #pragma unroll
       for (int b = 0; b < 16; ++b) { u1[b] = z[b].x; u2[b] = z[b].y; }
       // (u3, omega1)
-      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UZ, kx); x2 = Y(Y_WX, kx); }, z, ex, q, scale);
+      x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UZ, kx); x2 = Y(Y_WX, kx); }, z, ex, q, scale);
 #pragma unroll
       for (int b = 0; b < 16; ++b) {
         u3[b] = z[b].x;
         A1[b] = z[b].x * z[b].y;    // u3 omega1 (part of NL2)
         A2[b] = -u2[b] * z[b].y;    // -u2 omega1 (part of NL3)
         if (a.want_umax) {
-          const double s3 = (double)(fabs(u1[b]) + fabs(u2[b]) + fabs(u3[b]));
+          const double s3 = (double)(fabs(u1[b]) + fabs(u2[b]) + fabs(u3[b])) * (double)scale;
           umax = s3 > umax || s3 != s3 ? s3 : umax;
         }
       }
       // (omega2, omega3): omega2 = d_z u1 - i kx u3, omega3 = i kx u2 - d_y u1
-      x2inv<T, N>(
+      x2inv<T, N, false>(
           [&](int kx, C& x1, C& x2) {
             x1 = csub(Y(Y_DZUX, kx), mul_ik(Y(Y_UZ, kx), T(kx)));
             x2 = csub(mul_ik(Y(Y_UY, kx), T(kx)), Y(Y_DYUX, kx));
@@ -274,7 +298,7 @@ __global__ void __launch_bounds__(128, 3) k_xpass2(PassArgs a) {
 #pragma unroll
       for (int b = 0; b < 16; ++b) {
         const T w2 = z[b].x, w3 = z[b].y;
-        z[b] = mk(u2[b] * w3 - u3[b] * w2, A1[b] - u1[b] * w3);  // (NL1, NL2)
+        z[b] = mk((u2[b] * w3 - u3[b] * w2) * s2, (A1[b] - u1[b] * w3) * s2);  // (NL1, NL2)
         A2[b] += u1[b] * w2;                                     // NL3
       }
       x2fwd<T, N>(z,
@@ -284,14 +308,14 @@ __global__ void __launch_bounds__(128, 3) k_xpass2(PassArgs a) {
                   },
                   ex, q);
       // (dphi/dx1, dphi/dx2)
-      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_PHI, kx), T(kx)); x2 = Y(Y_DYPHI, kx); },
+      x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_PHI, kx), T(kx)); x2 = Y(Y_DYPHI, kx); },
                   z, ex, q, scale);
 #pragma unroll
       for (int b = 0; b < 16; ++b) A1[b] = u1[b] * z[b].x + u2[b] * z[b].y;
       // (dphi/dx3, 0)
-      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZPHI, kx); x2 = zero; }, z, ex, q, scale);
+      x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZPHI, kx); x2 = zero; }, z, ex, q, scale);
 #pragma unroll
-      for (int b = 0; b < 16; ++b) z[b] = mk(A2[b], A1[b] + u3[b] * z[b].x);  // (NL3, u.grad phi)
+      for (int b = 0; b < 16; ++b) z[b] = mk(A2[b] * s2, (A1[b] + u3[b] * z[b].x) * s2);  // (NL3, u.grad phi)
       x2fwd<T, N>(z,
                   [&](int kx, C X1, C X2) {
                     const long long i0 = 2 * ys + line * M + kx;
