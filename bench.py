@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=24)
     return ap.parse_args()
@@ -206,6 +207,38 @@ def run_ensemble(dev):
     out["speedup_vs_fp64_single_run"] = out["value"] / out["fp64_single_run"]["sims_per_hour_est"]
     torch.cuda.empty_cache()
     return out
+
+
+def run_cufft_comparator(dev, N):
+    """Library comparison (not the product): the 9 inverse and 4 forward 3D real
+    transforms one RHS evaluation needs, done with cuFFT through torch.fft on
+    full N^3 grids in FP32, timed with CUDA events.  No pointwise work, no
+    truncation, no projection: a lower bound for a plain cuFFT-based stage."""
+    import torch
+    torch.cuda.empty_cache()
+    try:
+        x = torch.randn(N, N, N, device=dev, dtype=torch.float32)
+        xh = torch.fft.rfftn(x)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(2):
+            torch.fft.irfftn(xh, s=(N, N, N))
+            torch.fft.rfftn(x)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(9):
+            y = torch.fft.irfftn(xh, s=(N, N, N))
+        for _ in range(4):
+            yh = torch.fft.rfftn(x)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        del x, xh, y, yh
+        torch.cuda.empty_cache()
+        return {"ms_per_stage_transforms": ms, "ms_per_step_transforms": 4 * ms,
+                "what": f"cuFFT via torch.fft: 9 irfftn + 4 rfftn of {N}^3 FP32 per RK stage"}
+    except Exception as e:
+        return {"error": str(e)[:200]}
 
 
 def run_serve(dev, n):
@@ -429,6 +462,9 @@ def main():
             torch.cuda.empty_cache()
         except Exception as e:  # report, do not hide
             out["fp64"] = {"error": str(e)[:200]}
+
+    if not a.no_cufft:
+        out["cufft_comparator"] = run_cufft_comparator(dev, N)
 
     if not a.no_ensemble:
         out["ensemble"] = run_ensemble(dev)

@@ -62,6 +62,8 @@ def build(checked: bool | None = None, jobs: int | None = None, verbose: bool = 
     flags = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC] + ARCH
     if checked:
         flags.append("-DPSC_CHECKED=1")
+    # developer knob for kernel-variant experiments, e.g. PSC_NVCC_FLAGS="-DPSC_X2_MIN_N=2048"
+    flags += os.environ.get("PSC_NVCC_FLAGS", "").split()
     tag = ("chk_" if checked else "") + _sources_digest(flags)
     odir = os.path.join(BUILD, tag)
     os.makedirs(odir, exist_ok=True)

@@ -321,7 +321,11 @@ template <typename T, int N> struct XCfg {
   static constexpr int STASH_REALS = STASH ? 3 * N : 0;
   static constexpr size_t LINE_BYTES =
       ((EXCH * sizeof(C) + STASH_REALS * sizeof(T)) + 15) / 16 * 16;
-  static constexpr size_t SMEM = LINE_BYTES * LPW * WARPS;
+  // twiddles of the inverse (wN^(n2 k1), n2 = t + j TPL < R2, k1 < R1) and of the
+  // transposed forward plan (n2 < R1, k1 < R2), each stored [j][k1][t] so the
+  // lanes of a row read consecutive entries
+  static constexpr size_t TW_BYTES = (size_t)2 * N * sizeof(C);
+  static constexpr size_t SMEM = LINE_BYTES * LPW * WARPS + TW_BYTES;
 };
 
 // Inverse DFT of one row from its half spectrum, two real fields at once:
@@ -333,7 +337,7 @@ template <typename T, int N, class SPEC>
 __device__ __forceinline__ void xinv(const SPEC& spec,
                                      typename CT<T>::type (&z)[PlanD<N>::J2][PlanD<N>::R2],
                                      typename CT<T>::type* ex,
-                                     const typename CT<T>::type* __restrict__ tw, int t, T scale) {
+                                     const typename CT<T>::type* tw, int t, T scale) {
   using C = typename CT<T>::type;
   using PL = PlanD<N>;
   using XC = XCfg<T, N>;
@@ -361,7 +365,7 @@ __device__ __forceinline__ void xinv(const SPEC& spec,
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       C v = a[k1];
-      if (k1 > 0) v = cmulc(v, tw[n2 * k1]);
+      if (k1 > 0) v = cmulc(v, tw[(j * R1 + k1) * TPL + t]);  // wN^(-n2 k1)
       ex[k1 * XC::ROWI + n2] = v;
     }
   }
@@ -384,7 +388,7 @@ __device__ __forceinline__ void xinv(const SPEC& spec,
 template <typename T, int N, class OUT>
 __device__ __forceinline__ void xfwd(typename CT<T>::type (&x)[PlanD<N>::J2][PlanD<N>::R2],
                                      const OUT& out, typename CT<T>::type* ex,
-                                     const typename CT<T>::type* __restrict__ tw, int t) {
+                                     const typename CT<T>::type* tw, int t) {
   using C = typename CT<T>::type;
   using PL = PlanD<N>;
   using XC = XCfg<T, N>;
@@ -397,7 +401,7 @@ __device__ __forceinline__ void xfwd(typename CT<T>::type (&x)[PlanD<N>::J2][Pla
 #pragma unroll
     for (int k1 = 0; k1 < R2; ++k1) {
       C v = x[j][k1];
-      if (k1 > 0) v = cmul(v, tw[n2 * k1]);
+      if (k1 > 0) v = cmul(v, tw[N + (j * R2 + k1) * TPL + t]);  // wN^(n2 k1)
       ex[k1 * XC::ROWF + n2] = v;
     }
   }
@@ -447,7 +451,18 @@ k_xpass(PassArgs a) {
   T* stash = reinterpret_cast<T*>(myline + XC::EXCH * sizeof(C));
   const C* __restrict__ yb = static_cast<const C*>(a.yb);
   C* __restrict__ xb = static_cast<C*>(a.xb);
-  const C* __restrict__ tw = static_cast<const C*>(a.tw);
+  C* tw = reinterpret_cast<C*>(smraw + XC::LINE_BYTES * LPW * XC::WARPS);
+  {
+    const C* __restrict__ twg = static_cast<const C*>(a.tw);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const int tt = i % TPL;
+      const int k1i = (i / TPL) % R1, ji = i / (TPL * R1);  // inverse: k1 < R1, j < J1
+      tw[i] = twg[(tt + ji * TPL) * k1i];
+      const int k1f = (i / TPL) % R2, jf = i / (TPL * R2);  // forward: k1 < R2, j < J2
+      tw[N + i] = twg[(tt + jf * TPL) * k1f];
+    }
+    __syncthreads();
+  }
   const long long ys = (long long)N * N * M;
   const long long nlines = (long long)N * N;
   const T scale = T(1.0 / ((double)N * N * N));
@@ -694,7 +709,10 @@ template <typename T, int N> struct Passes {
   static constexpr size_t SSMZ = StridedSmem<T, N, WZ>::BYTES, SSMY = StridedSmem<T, N, WY>::BYTES;
 
   // rows of N = 512 and 1024 use the 16-values-per-thread layout of psc_xpass2.cuh
-  static constexpr bool X2 = (N == 512 || N == 1024);
+#ifndef PSC_X2_MIN_N
+#define PSC_X2_MIN_N 512
+#endif
+  static constexpr bool X2 = (N == 512 || N == 1024) && N >= PSC_X2_MIN_N;
 
   static int xgrid() {
     if constexpr (X2) {

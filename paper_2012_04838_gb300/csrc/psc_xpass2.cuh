@@ -214,7 +214,10 @@ __device__ __forceinline__ double warp_sum_d(T v) {
 }
 
 template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(128, 3) k_xpass2(PassArgs a) {
+#ifndef PSC_X2_MINB
+#define PSC_X2_MINB 4
+#endif
+__global__ void __launch_bounds__(128, PSC_X2_MINB) k_xpass2(PassArgs a) {
   using C = typename CT<T>::type;
   using XC = X2Cfg<T, N>;
   constexpr int TH = XC::TH, G = XC::G, ROWS = XC::ROWS, M = XC::K + 1;
