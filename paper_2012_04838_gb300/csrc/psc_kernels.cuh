@@ -200,9 +200,11 @@ __device__ __forceinline__ double block_sum(double v, double* sm) {
   return s;
 }
 
+// floor(sqrt(a)) for 0 <= a < 2^46: an FP32 estimate corrected in integers
+// (exact; the FP64 square root is slow on this part)
 __device__ __forceinline__ long long isqrt_floor(long long a) {
   if (a <= 0) return 0;
-  long long s = (long long)sqrt((double)a);
+  long long s = (long long)sqrtf((float)a);
   while (s * s > a) --s;
   while ((s + 1) * (s + 1) <= a) ++s;
   return s;

@@ -256,10 +256,9 @@ __global__ void __launch_bounds__(128, PSC_X2_MINB) k_xpass2(PassArgs a) {
   const T scale = T(1.0 / ((double)N * N * N));
   const C zero = mk(T(0), T(0));
   double umax = 0.0;
-  if (MODE == XMODE_STATS) {
-    for (int i = lane; i < NQ; i += 32) accw[i] = 0.0;
-    __syncwarp();
-  }
+  double acc[MODE == XMODE_STATS ? NQ : 1];
+#pragma unroll
+  for (int i = 0; i < (MODE == XMODE_STATS ? NQ : 1); ++i) acc[i] = 0.0;
 
 #pragma unroll 1
   for (long long base = (long long)blockIdx.x * ROWS; base < nlines; base += (long long)gridDim.x * ROWS) {
@@ -326,13 +325,11 @@ __global__ void __launch_bounds__(128, PSC_X2_MINB) k_xpass2(PassArgs a) {
                   },
                   ex, q);
     } else {
-      // statistics (Eqs. 11-13): per pair, FP32/FP64 partial sums of the thread's
-      // 16 points, reduced over the warp in FP64 into the warp's accumulators
+      // statistics (Eqs. 11-13): per pair, partial sums of the thread's 16
+      // points, added in FP64 to the thread's accumulators (reduced over the
+      // warp once, at the end)
       T s13[16];
-      auto put = [&](int slot, T v) {
-        const double d = warp_sum_d<T>(v);
-        if (lane == 0) accw[slot] += d;
-      };
+      auto put = [&](int slot, T v) { acc[slot] += (double)v; };
       auto mom3 = [&](int slot, const T (&f)[16]) {
         T m2 = T(0), m3 = T(0), m4 = T(0);
 #pragma unroll
@@ -418,10 +415,14 @@ __global__ void __launch_bounds__(128, PSC_X2_MINB) k_xpass2(PassArgs a) {
     if (lane == 0) atomicMax(&a.ctrl->umax_bits, (unsigned long long)__double_as_longlong(umax));
   }
   if constexpr (MODE == XMODE_STATS) {
-    __syncwarp();
     const long long gw = (long long)blockIdx.x * 4 + wid;
-    for (int i = lane; i < NQ; i += 32) a.partials[gw * NQ + i] = accw[i];
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+      const double v = warp_sum_d<double>(acc[i]);
+      if (lane == 0) a.partials[gw * NQ + i] = v;
+    }
   }
+  (void)accw;
 }
 
 }  // namespace psc
