@@ -51,6 +51,23 @@ def parse():
 
 # ---------------------------------------------------------------- helpers
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest value of x over all ranks (the slowest replica sets the time)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(steps_per_rank: int, world: int, ms_max: float) -> float:
+    """Replicas only: every rank steps its own box, so the job advances
+    world * steps box-steps in the slowest rank's time."""
+    return world * steps_per_rank / (ms_max / 1000.0)
+
+
 def kernel_bytes(N: int, cbytes: int) -> dict:
     """Algorithmic bytes per launch of each kernel kind (reads + writes of the
     minimum data each pass must move; complex elements of `cbytes` bytes)."""
@@ -356,11 +373,8 @@ def main():
     prof = sim.profile_read()
     sim.profile(False)
     last_rec, _, _ = sim.stats()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * a.steps / (ms / 1000.0)
+    ms = max_over_ranks(ms, world, dev)
+    value = whole_job_rate(a.steps, world, ms)
 
     # roofline of the dominant kernel (per-launch device time from CUDA events)
     kb = kernel_bytes(N, 8)
@@ -425,11 +439,7 @@ def main():
         st = sim.lib.psc_get_state(sim._h, back.data_ptr(), sim.state_bytes())
         if st != 0:
             raise RuntimeError("psc_get_state failed")
-        el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(time.perf_counter() - t0, world, dev)
         rec_bytes = 37 * 8 + 2 * 8 * 600
         out["e2e"] = {"value": world * a.steps / el, "unit": "steps/s",
                       "h2d_bytes_per_step": sim.state_bytes() / a.steps,

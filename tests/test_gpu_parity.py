@@ -227,3 +227,28 @@ def test_state_roundtrip_and_restart_are_bit_exact(dev, prec):
 def test_unsupported_and_short_workspace(dev):
     with pytest.raises(B.PscError):
         B.Simulation(B.Params(N=100), device=dev)
+
+
+@pytest.mark.parametrize("prec", PREC, ids=PNAME.get)
+def test_nonfinite_state_is_reported_unstable(dev, prec):
+    # failure injected on the host: a non-finite mode in an otherwise valid state
+    N = 16
+    x = random_compact_state(N, 3)
+    K = (N - 1) // 3
+    x[1, K + 2, K - 1, 3] = np.nan
+    p = B.Params(N=N, precision=prec, cfl=0.5)
+    sim = B.Simulation(p, device=dev)
+    sim.set_state(torch.from_numpy(x))
+    with pytest.raises(B.PscError) as e:
+        sim.stats()
+    assert e.value.status == B.PSC_EUNSTABLE
+    # a CFL-controlled step from it raises the device flag; the context stays usable
+    sim.step(1)
+    with pytest.raises(B.PscError) as e:
+        sim.stats()
+    assert e.value.status == B.PSC_EUNSTABLE
+    ok = B.Simulation(B.Params(N=N, precision=prec), device=dev)
+    ok.init_field()
+    ok.step(1)
+    rec, _, _ = ok.stats()
+    assert np.isfinite(rec["K"])
