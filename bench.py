@@ -80,8 +80,9 @@ def kernel_bytes(N: int, cbytes: int) -> dict:
         "xpass": (9 * ys + 4 * ys) * cbytes,
         "yfwd": (4 * ys + 4 * zs) * cbytes,
         "zfwd": (4 * zs + 4 * S) * cbytes,
-        # stage updates: 16 S (stages 1, 4) and 24 S (stages 2, 3) complex values
-        "combine": 20 * S * cbytes,
+        # stage updates (complex values): 16 S at stage 1, 21 S at stages 2-3,
+        # 13 S at stage 4 (the stage input is read in full only on the band)
+        "combine": 71 * S * cbytes // 4,
     }
 
 
@@ -417,7 +418,8 @@ def main():
            "step_roofline": {"algorithmic_bytes_per_step": step_bytes,
                              "achieved_GBps": round(step_bytes / (ms / a.steps / 1000.0) / 1e9, 1),
                              "frac": round(step_bytes / (ms / a.steps / 1000.0) / 1e9 / peak, 4)},
-           "kernels": per_kernel, "gpu_launches": launches, "clocks": clk.summary(),
+           "kernels": per_kernel, "tile_widths": sim.tile_widths(), "gpu_launches": launches,
+           "clocks": clk.summary(),
            "last_record": {k: last_rec[k] for k in ("t", "dt", "K", "eps", "Re_lambda", "kmax_eta", "cfl",
                                                     "phi_var", "chi")}}
 

@@ -181,6 +181,13 @@ typedef enum {
 psc_status psc_profile_enable(psc_sim* s, int32_t on);
 psc_status psc_profile_read(psc_sim* s, double* ms, int64_t* launches, int32_t nkind);
 
+/* Column tile widths chosen for the four strided passes (z-inverse, y-inverse,
+ * y-forward, z-forward; w receives 4 values).  psc_create() times the compiled
+ * widths of each FP32 pass on the simulation's workspace and keeps the fastest
+ * (cached per grid size for the process; PSC_TUNE=0 in the environment keeps
+ * fixed defaults instead). */
+psc_status psc_tile_widths(const psc_sim* s, int32_t* w);
+
 /* Total kernels this simulation has launched since creation (always counted). */
 psc_status psc_launch_count(const psc_sim* s, int64_t* n);
 

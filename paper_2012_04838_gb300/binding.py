@@ -74,6 +74,7 @@ EXPORTS = [
     ("psc_profile_enable", ct.c_int, [_VP, ct.c_int32]),
     ("psc_profile_read", ct.c_int, [_VP, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.c_int32]),
     ("psc_launch_count", ct.c_int, [_VP, ct.POINTER(ct.c_int64)]),
+    ("psc_tile_widths", ct.c_int, [_VP, ct.POINTER(ct.c_int32)]),
     ("psc_destroy", ct.c_int, [_VP]),
     ("psc_shell_spectra_noalloc", ct.c_int, [_VP, ct.c_int32, ct.c_int32, ct.POINTER(ct.c_double),
                                              ct.POINTER(ct.c_double), ct.c_int32, _VP]),
@@ -257,6 +258,11 @@ class Simulation:
         cnt = (ct.c_int64 * n)()
         _check(self.lib, self.lib.psc_profile_read(self._h, ms, cnt, n))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(self.KERNEL_KINDS)}
+
+    def tile_widths(self) -> dict:
+        w = (ct.c_int32 * 4)()
+        _check(self.lib, self.lib.psc_tile_widths(self._h, w))
+        return dict(zip(("zinv", "yinv", "yfwd", "zfwd"), list(w)))
 
     def launch_count(self) -> int:
         n = ct.c_int64()

@@ -1,8 +1,12 @@
 // Host side of the C ABI (include/psc.h): parameter checks, workspace
 // layout, stage orchestration and assembly of the statistics record.
+#include <array>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -149,6 +153,7 @@ struct psc_sim {
   Ctrl* ctrl;
   int64_t step;
   int nshell;
+  int wv[SP_N];  // tile-width variant of each strided pass (autotuned at creation)
   // launch accounting and optional per-launch event timing
   int64_t launches = 0;
   bool profiling = false;
@@ -207,6 +212,7 @@ static const PassTable* pick_table(const psc_params* p) {
 
 namespace {
 template <typename T> void launch_iftab(psc_sim* s);
+psc_status autotune(psc_sim* s);
 }
 
 extern "C" {
@@ -275,6 +281,11 @@ psc_status psc_create(const psc_params* p, void* dev_ws, size_t ws_bytes, void* 
     delete sim;
     return cuda_fail(e, "psc_create");
   }
+  psc_status ts = autotune(sim);
+  if (ts != PSC_OK) {
+    delete sim;
+    return ts;
+  }
   *out = sim;
   return PSC_OK;
 }
@@ -315,6 +326,12 @@ psc_status psc_profile_read(psc_sim* s, double* ms, int64_t* launches, int32_t n
     if (ms) ms[k] = t[k];
     if (launches) launches[k] = n[k];
   }
+  return PSC_OK;
+}
+
+psc_status psc_tile_widths(const psc_sim* s, int32_t* w) {
+  if (!s || !w) return fail(PSC_EINVAL, "null argument");
+  for (int p = 0; p < SP_N; ++p) w[p] = s->tb->widths[s->wv[p]];
   return PSC_OK;
 }
 
@@ -414,8 +431,8 @@ void rhs_passes(psc_sim* s, const void* in, bool umax) {
   a.want_umax = umax ? 1 : 0;
   if (umax) cudaMemsetAsync(&s->ctrl->umax_bits, 0, sizeof(unsigned long long), s->st);
   launch_famp<T>(s, in);
-  launch(s, PSC_K_ZINV, 1, [&] { s->tb->zinv(a, false); });
-  launch(s, PSC_K_YINV, 1, [&] { s->tb->yinv(a, false); });
+  launch(s, PSC_K_ZINV, 1, [&] { s->tb->zinv(a, false, s->wv[SP_ZINV]); });
+  launch(s, PSC_K_YINV, 1, [&] { s->tb->yinv(a, false, s->wv[SP_YINV]); });
   launch(s, PSC_K_XPASS, 1, [&] { s->tb->xpass(a, XMODE_RHS); });
   if (umax && s->p.cfl > 0.0) {
     launch(s, PSC_K_OTHER, 1, [&] {
@@ -423,8 +440,8 @@ void rhs_passes(psc_sim* s, const void* in, bool umax) {
     });
     launch_iftab<T>(s);
   }
-  launch(s, PSC_K_YFWD, 1, [&] { s->tb->yfwd(a); });
-  launch(s, PSC_K_ZFWD, 1, [&] { s->tb->zfwd(a); });
+  launch(s, PSC_K_YFWD, 1, [&] { s->tb->yfwd(a, s->wv[SP_YFWD]); });
+  launch(s, PSC_K_ZFWD, 1, [&] { s->tb->zfwd(a, s->wv[SP_ZFWD]); });
 }
 
 template <typename T>
@@ -492,8 +509,8 @@ psc_status do_stats(psc_sim* s, double* Ek, double* Ephi, int cap, int* nshell, 
   PSC_CUDA(cudaMemsetAsync(&s->ctrl->umax_bits, 0, sizeof(unsigned long long), s->st));
   launch_famp<T>(s, U);
   launch(s, PSC_K_OTHER, 3, [&] {
-    s->tb->zinv(a, true);
-    s->tb->yinv(a, true);
+    s->tb->zinv(a, true, s->wv[SP_ZINV]);
+    s->tb->yinv(a, true, s->wv[SP_YINV]);
     s->tb->xpass(a, XMODE_STATS);
   });
   double* shells = (double*)(s->ws + s->L.shells);
@@ -572,6 +589,77 @@ psc_status do_stats(psc_sim* s, double* Ek, double* Ephi, int cap, int* nshell, 
   (void)Vp;
   if ((c.err & 2) || !(umax <= 1.7976931348623157e308))
     return fail(PSC_EUNSTABLE, "non-finite velocity in the CFL monitor");
+  return PSC_OK;
+}
+
+// Tile-width autotuner of the strided passes.  Both compiled widths of each
+// pass are timed on this simulation's own workspace (one warm-up and three
+// timed launches each, CUDA events on its stream) and the faster is kept.
+// Choices are cached per (grid size, precision) for the life of the process,
+// so ensembles and servers tune once per N.  PSC_TUNE=0 in the environment
+// skips the timing and uses 128-byte runs (16 columns) for the z passes and for
+// N < 512, 64-byte runs for the y passes at N >= 512.
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, std::array<int, SP_N>> g_tune_cache;
+
+psc_status autotune(psc_sim* s) {
+  const int N = s->d.N;
+  for (int p = 0; p < SP_N; ++p) s->wv[p] = 0;
+  if (s->tb->nvariants < 2) return PSC_OK;
+  const bool ypass_narrow = N >= 512;
+  s->wv[SP_ZINV] = 1;
+  s->wv[SP_ZFWD] = 1;
+  s->wv[SP_YINV] = ypass_narrow ? 0 : 1;
+  s->wv[SP_YFWD] = ypass_narrow ? 0 : 1;
+  const char* env = std::getenv("PSC_TUNE");
+  if (env && env[0] == '0') return PSC_OK;
+  const std::pair<int, int> key(N, s->fp64);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      for (int p = 0; p < SP_N; ++p) s->wv[p] = it->second[p];
+      return PSC_OK;
+    }
+  }
+  PassArgs a = pass_args(s, s->ws + s->L.U);
+  cudaEvent_t e0, e1;
+  PSC_CUDA(cudaEventCreate(&e0));
+  PSC_CUDA(cudaEventCreate(&e1));
+  auto run = [&](int p, int v) {
+    switch (p) {
+      case SP_ZINV: s->tb->zinv(a, false, v); break;
+      case SP_YINV: s->tb->yinv(a, false, v); break;
+      case SP_YFWD: s->tb->yfwd(a, v); break;
+      default: s->tb->zfwd(a, v); break;
+    }
+  };
+  std::array<int, SP_N> best;
+  cudaError_t e = cudaSuccess;
+  for (int p = 0; p < SP_N && e == cudaSuccess; ++p) {
+    float tbest = 0.f;
+    best[p] = s->wv[p];
+    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+      run(p, v);
+      cudaEventRecord(e0, s->st);
+      for (int r = 0; r < 3; ++r) run(p, v);
+      cudaEventRecord(e1, s->st);
+      e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && (v == 0 || ms < tbest)) {
+        tbest = ms;
+        best[p] = v;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "psc_create: tile autotuning");
+  for (int p = 0; p < SP_N; ++p) s->wv[p] = best[p];
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache[key] = best;
   return PSC_OK;
 }
 

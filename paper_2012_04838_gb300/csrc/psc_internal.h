@@ -70,13 +70,18 @@ struct PassArgs {
 
 enum { XMODE_RHS = 0, XMODE_STATS = 1 };
 
+// Strided passes come in tile-width variants v (index into widths[]).
+enum { SP_ZINV = 0, SP_YINV = 1, SP_YFWD = 2, SP_ZFWD = 3, SP_N = 4 };
+
 struct PassTable {
-  void (*zinv)(const PassArgs&, bool stats);
-  void (*yinv)(const PassArgs&, bool stats);
+  void (*zinv)(const PassArgs&, bool stats, int v);
+  void (*yinv)(const PassArgs&, bool stats, int v);
   void (*xpass)(const PassArgs&, int mode);
-  void (*yfwd)(const PassArgs&);
-  void (*zfwd)(const PassArgs&);
+  void (*yfwd)(const PassArgs&, int v);
+  void (*zfwd)(const PassArgs&, int v);
   int xwarps;       // warps launched by the X pass (rows of `partials`)
+  int nvariants;    // tile-width variants of the strided passes (1 or 2)
+  int widths[2];    // their column tile widths
 };
 
 const PassTable* table_f32(int N);

@@ -65,9 +65,15 @@ __global__ void __launch_bounds__(256) k_combine(CombineArgs c) {
   } else {
     r0 = r1 = r2 = mk(T(0), T(0));
   }
-  const C v0 = vin[i], v1 = vin[S + i], v2 = vin[2 * S + i], v3 = vin[3 * S + i];
+  // the stage input is needed in full only on the forcing band and for the
+  // explicit linear terms of plain RK4; elsewhere only u2 (scalar source)
+  const bool band = c.forcing && k2 > 0 && (double)k2 <= c.kF2;
+  const bool all = band || c.integrator == 1;
+  const C zero = mk(T(0), T(0));
+  const C v1 = vin[S + i];
+  const C v0 = all ? vin[i] : zero, v2 = all ? vin[2 * S + i] : zero, v3 = all ? vin[3 * S + i] : zero;
   // constant-power forcing A u on 0 < |k|^2 <= kF^2
-  if (c.forcing && k2 > 0 && (double)k2 <= c.kF2) {
+  if (band) {
     const T A = (T)c.ctrl->A;
     r0 = mk(r0.x + A * v0.x, r0.y + A * v0.y);
     r1 = mk(r1.x + A * v1.x, r1.y + A * v1.y);

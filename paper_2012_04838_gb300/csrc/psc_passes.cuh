@@ -28,12 +28,10 @@ namespace psc {
 // W-wide contiguous run of complex values.
 // ---------------------------------------------------------------------------
 
-// Column tile width per pass (measured on GB300 at 512^3 and 1024^3 in FP32:
-// 128-byte runs pay off for the z passes, 64-byte runs with two CTAs per SM
-// for the y passes).
-enum { PASS_Z = 0, PASS_Y = 1 };
-template <typename T, int N, int AXIS = PASS_Z> struct StridedCfg {
-  static constexpr int W = (sizeof(T) == 4) ? ((N >= 512 && AXIS == PASS_Y) ? 8 : 16) : 8;
+// Column tile width: FP32 passes are built for W = 8 and 16 (64- and 128-byte
+// runs) and the faster is picked per pass and grid size when a simulation is
+// created (see psc_capi.cu); FP64 uses W = 8.
+template <typename T, int N, int W> struct StridedCfg {
   static constexpr int THREADS = W * PlanD<N>::TPL;
   // FP32: cap registers at 128 per thread so at least 512 threads fit on an SM;
   // FP64 is bound by the FP64 pipe, so it keeps its values in registers instead
@@ -125,11 +123,11 @@ template <int N> __device__ __forceinline__ bool k_of_pos(int p, int& k) {
 // Each kernel runs its transforms through one copy of the transform code (a
 // runtime loop over its stream table), so the instruction footprint stays that
 // of a single two-step FFT however many streams the pass carries.
-template <typename T, int N, bool STATS>
-__global__ void __launch_bounds__(StridedCfg<T, N, PASS_Z>::THREADS, StridedCfg<T, N, PASS_Z>::MINB)
+template <typename T, int N, bool STATS, int W>
+__global__ void __launch_bounds__(StridedCfg<T, N, W>::THREADS, StridedCfg<T, N, W>::MINB)
 k_zinv(PassArgs a) {
   using C = typename CT<T>::type;
-  constexpr int W = StridedCfg<T, N, PASS_Z>::W, K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
+  constexpr int K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int w = threadIdx.x, t = threadIdx.y;
@@ -176,11 +174,11 @@ k_zinv(PassArgs a) {
   }
 }
 
-template <typename T, int N, bool STATS>
-__global__ void __launch_bounds__(StridedCfg<T, N, PASS_Y>::THREADS, StridedCfg<T, N, PASS_Y>::MINB)
+template <typename T, int N, bool STATS, int W>
+__global__ void __launch_bounds__(StridedCfg<T, N, W>::THREADS, StridedCfg<T, N, W>::MINB)
 k_yinv(PassArgs a) {
   using C = typename CT<T>::type;
-  constexpr int W = StridedCfg<T, N, PASS_Y>::W, K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
+  constexpr int K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int w = threadIdx.x, t = threadIdx.y;
@@ -233,11 +231,11 @@ k_yinv(PassArgs a) {
   }
 }
 
-template <typename T, int N>
-__global__ void __launch_bounds__(StridedCfg<T, N, PASS_Y>::THREADS, StridedCfg<T, N, PASS_Y>::MINB)
+template <typename T, int N, int W>
+__global__ void __launch_bounds__(StridedCfg<T, N, W>::THREADS, StridedCfg<T, N, W>::MINB)
 k_yfwd(PassArgs a) {
   using C = typename CT<T>::type;
-  constexpr int W = StridedCfg<T, N, PASS_Y>::W, K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
+  constexpr int K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int w = threadIdx.x, t = threadIdx.y;
@@ -268,11 +266,11 @@ k_yfwd(PassArgs a) {
   }
 }
 
-template <typename T, int N>
-__global__ void __launch_bounds__(StridedCfg<T, N, PASS_Z>::THREADS, StridedCfg<T, N, PASS_Z>::MINB)
+template <typename T, int N, int W>
+__global__ void __launch_bounds__(StridedCfg<T, N, W>::THREADS, StridedCfg<T, N, W>::MINB)
 k_zfwd(PassArgs a) {
   using C = typename CT<T>::type;
-  constexpr int W = StridedCfg<T, N, PASS_Z>::W, K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
+  constexpr int K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int w = threadIdx.x, t = threadIdx.y;
@@ -703,10 +701,10 @@ namespace psc {
 // ---------------------------------------------------------------------------
 
 template <typename T, int N> struct Passes {
-  static constexpr int WZ = StridedCfg<T, N, PASS_Z>::W, WY = StridedCfg<T, N, PASS_Y>::W;
   static constexpr int TPL = PlanD<N>::TPL;
   static constexpr int M = PlanD<N>::M, P = PlanD<N>::P;
-  static constexpr size_t SSMZ = StridedSmem<T, N, WZ>::BYTES, SSMY = StridedSmem<T, N, WY>::BYTES;
+  // tile widths of the two variants (v = 0, 1)
+  static constexpr int WV0 = 8, WV1 = sizeof(T) == 4 ? 16 : 8;
 
   // rows of N = 512 and 1024 use the 16-values-per-thread layout of psc_xpass2.cuh
 #ifndef PSC_X2_MIN_N
@@ -731,16 +729,34 @@ template <typename T, int N> struct Passes {
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
 
-  static void zinv(const PassArgs& a, bool stats) {
-    dim3 grid((M + WZ - 1) / WZ, P), block(WZ, TPL);
-    if (stats) { prep(k_zinv<T, N, true>, SSMZ); k_zinv<T, N, true><<<grid, block, SSMZ, a.st>>>(a); }
-    else { prep(k_zinv<T, N, false>, SSMZ); k_zinv<T, N, false><<<grid, block, SSMZ, a.st>>>(a); }
+  template <int W> static void zinv_w(const PassArgs& a, bool stats) {
+    constexpr size_t sm = StridedSmem<T, N, W>::BYTES;
+    dim3 grid((M + W - 1) / W, P), block(W, TPL);
+    if (stats) { prep(k_zinv<T, N, true, W>, sm); k_zinv<T, N, true, W><<<grid, block, sm, a.st>>>(a); }
+    else { prep(k_zinv<T, N, false, W>, sm); k_zinv<T, N, false, W><<<grid, block, sm, a.st>>>(a); }
   }
-  static void yinv(const PassArgs& a, bool stats) {
-    dim3 grid((M + WY - 1) / WY, N), block(WY, TPL);
-    if (stats) { prep(k_yinv<T, N, true>, SSMY); k_yinv<T, N, true><<<grid, block, SSMY, a.st>>>(a); }
-    else { prep(k_yinv<T, N, false>, SSMY); k_yinv<T, N, false><<<grid, block, SSMY, a.st>>>(a); }
+  template <int W> static void yinv_w(const PassArgs& a, bool stats) {
+    constexpr size_t sm = StridedSmem<T, N, W>::BYTES;
+    dim3 grid((M + W - 1) / W, N), block(W, TPL);
+    if (stats) { prep(k_yinv<T, N, true, W>, sm); k_yinv<T, N, true, W><<<grid, block, sm, a.st>>>(a); }
+    else { prep(k_yinv<T, N, false, W>, sm); k_yinv<T, N, false, W><<<grid, block, sm, a.st>>>(a); }
   }
+  template <int W> static void yfwd_w(const PassArgs& a) {
+    constexpr size_t sm = StridedSmem<T, N, W>::BYTES;
+    dim3 grid((M + W - 1) / W, N), block(W, TPL);
+    prep(k_yfwd<T, N, W>, sm);
+    k_yfwd<T, N, W><<<grid, block, sm, a.st>>>(a);
+  }
+  template <int W> static void zfwd_w(const PassArgs& a) {
+    constexpr size_t sm = StridedSmem<T, N, W>::BYTES;
+    dim3 grid((M + W - 1) / W, P), block(W, TPL);
+    prep(k_zfwd<T, N, W>, sm);
+    k_zfwd<T, N, W><<<grid, block, sm, a.st>>>(a);
+  }
+  static void zinv(const PassArgs& a, bool stats, int v) { v ? zinv_w<WV1>(a, stats) : zinv_w<WV0>(a, stats); }
+  static void yinv(const PassArgs& a, bool stats, int v) { v ? yinv_w<WV1>(a, stats) : yinv_w<WV0>(a, stats); }
+  static void yfwd(const PassArgs& a, int v) { v ? yfwd_w<WV1>(a) : yfwd_w<WV0>(a); }
+  static void zfwd(const PassArgs& a, int v) { v ? zfwd_w<WV1>(a) : zfwd_w<WV0>(a); }
   static void xpass(const PassArgs& a, int mode) {
     if constexpr (X2) {
       const size_t sm2 = X2Cfg<T, N>::SMEM;
@@ -763,19 +779,10 @@ template <typename T, int N> struct Passes {
       }
     }
   }
-  static void yfwd(const PassArgs& a) {
-    dim3 grid((M + WY - 1) / WY, N), block(WY, TPL);
-    prep(k_yfwd<T, N>, SSMY);
-    k_yfwd<T, N><<<grid, block, SSMY, a.st>>>(a);
-  }
-  static void zfwd(const PassArgs& a) {
-    dim3 grid((M + WZ - 1) / WZ, P), block(WZ, TPL);
-    prep(k_zfwd<T, N>, SSMZ);
-    k_zfwd<T, N><<<grid, block, SSMZ, a.st>>>(a);
-  }
   static const PassTable* table() {
     static const PassTable tb = {&zinv, &yinv, &xpass, &yfwd, &zfwd,
-                                 xgrid() * (X2 ? 4 : XCfg<T, N>::WARPS)};
+                                 xgrid() * (X2 ? 4 : XCfg<T, N>::WARPS), WV0 != WV1 ? 2 : 1,
+                                 {WV0, WV1}};
     return &tb;
   }
 };
