@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-cufft", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--long-run", action="store_true",
+                    help="only run 256^3 FP32-mixed and FP64 side by side for 2000 steps and "
+                         "print their statistical agreement")
     return ap.parse_args()
 
 
@@ -314,10 +317,56 @@ def run_reference(a):
 
 # ---------------------------------------------------------------- our arm
 
+def run_long(N=256, steps=2000, every=10):
+    """FP32-mixed and FP64 from the same IC, side by side: time-averaged E(k)
+    (second half of the run) per shell for k <= k_max/2 and dissipation."""
+    import numpy as np
+    import torch
+    import paper_2012_04838_gb300 as psc
+    from paper_2012_04838_gb300.serve import nu_for_resolution
+    out = {"N": N, "steps": steps, "record_every": every}
+    res = {}
+    for name, prec in (("fp32_mixed", psc.FP32_MIXED), ("fp64", psc.FP64)):
+        p = psc.Params(N=N, precision=prec, nu=nu_for_resolution(N, 1.5), Sc=1.0, beta=1.0, kF=2.0,
+                       eps_inj=0.1, cfl=0.5, ic=psc.IC_SPECTRUM_K4, seed=2, ic_energy=1.5,
+                       record_every=every)
+        sim = psc.Simulation(p, device="cuda:0")
+        sim.init_field()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        recs, spec = [], []
+        for n in range(0, steps + 1, every):
+            if n:
+                sim.step(every)
+            r, E, _ = sim.stats()
+            recs.append(r)
+            spec.append(E)
+        out[name + "_wall_s"] = time.perf_counter() - t0
+        res[name] = (recs, np.array(spec))
+        sim.close()
+        torch.cuda.empty_cache()
+    half = (steps // every + 1) // 2
+    r32, E32 = res["fp32_mixed"]
+    r64, E64 = res["fp64"]
+    e32 = float(np.mean([r["eps"] for r in r32[half:]]))
+    e64 = float(np.mean([r["eps"] for r in r64[half:]]))
+    kh = int((N / 3) / 2)
+    m32, m64 = E32[half:].mean(axis=0), E64[half:].mean(axis=0)
+    rel = np.abs(m32[1:kh + 1] - m64[1:kh + 1]) / m64[1:kh + 1]
+    out.update({"eps_fp32": e32, "eps_fp64": e64, "eps_rel_diff": abs(e32 - e64) / e64,
+                "E_max_rel_diff_k_le_kmax_over_2": float(rel.max()), "shells_compared": kh,
+                "t_end": r64[-1]["t"], "Re_lambda_end": r64[-1]["Re_lambda"],
+                "final_state_rel_diff_K": abs(r32[-1]["K"] - r64[-1]["K"]) / r64[-1]["K"]})
+    return out
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.long_run:
+        print(json.dumps({"long_run": run_long()}), flush=True)
+        return 0
 
     import torch
     import torch.distributed as dist
