@@ -44,7 +44,8 @@ typedef enum {
   PSC_ENOMEM_BUDGET = 2,   /* workspace smaller than psc_workspace_size()         */
   PSC_ECUDA = 3,           /* a CUDA runtime call failed (see psc_last_error)     */
   PSC_EUNSTABLE = 4,       /* non-finite velocity seen by the CFL monitor (Eq. 10)*/
-  PSC_ETIMEOUT = 5,        /* reserved: a bounded device wait gave up             */
+  PSC_ETIMEOUT = 5,        /* a bounded device wait gave up (reported at the next
+                              statistics call)                                     */
   PSC_EUNSUPPORTED_N = 6   /* N outside the supported set of grid sizes           */
 } psc_status;
 

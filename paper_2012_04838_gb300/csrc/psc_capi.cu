@@ -399,6 +399,7 @@ CombineArgs combine_args(psc_sim* s, const void* vin) {
   c.ep = s->ws + s->L.ep;
   c.ctrl = s->ctrl;
   c.kF2 = s->p.kF * s->p.kF;
+  c.kF2_floor = c.kF2 >= 2.0e9 ? 2000000000 : (int)std::floor(c.kF2);
   c.beta = s->p.beta;
   c.nu = s->p.nu;
   c.D = s->p.nu / s->p.Sc;
@@ -589,6 +590,7 @@ psc_status do_stats(psc_sim* s, double* Ek, double* Ephi, int cap, int* nshell, 
   (void)Vp;
   if ((c.err & 2) || !(umax <= 1.7976931348623157e308))
     return fail(PSC_EUNSTABLE, "non-finite velocity in the CFL monitor");
+  if (c.err & 4) return fail(PSC_ETIMEOUT, "an asynchronous copy into shared memory did not complete in time");
   return PSC_OK;
 }
 

@@ -87,6 +87,92 @@ __host__ __device__ constexpr int band_of(int N, int TH, int m) {
                                                                       : 2;
 }
 
+// Per-thread running sum of one statistics moment.  The FP64 path sums in
+// FP64; the FP32 path keeps a compensated FP32 sum (Kahan 1965: the rounding
+// error of each addition is carried into the next), whose error stays within
+// a few units of FP32 rounding of the sum of magnitudes however many terms it
+// takes, at FP32 cost (FP64 arithmetic runs at a small fraction of the FP32
+// rate on this part).
+template <typename T> struct MomentSum;
+template <> struct MomentSum<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct MomentSum<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// running maximum that keeps a NaN once one is seen
+template <typename T> __device__ __forceinline__ T max_keep_nan(T m, T v) {
+  return v > m || v != v ? v : m;
+}
+
+// Bulk asynchronous copies (TMA engine) into shared memory, completed on an
+// mbarrier.  A wait gives up after a bounded number of polls and reports it.
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+// make barrier initialisation visible to the asynchronous proxy
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// order this thread's earlier shared-memory accesses (and those the last
+// barrier made visible to it) before later asynchronous-proxy writes
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes)
+               : "memory");
+}
+// global -> shared copy of `bytes` (multiple of 16; both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes,
+                                              unsigned long long* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(b))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// wait for the phase of parity `parity` to complete; false after ~2^22 polls
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity) {
+  for (int i = 0; i < (1 << 22); ++i)
+    if (mbar_try_wait(b, parity)) return true;
+  return false;
+}
+// AND of `pred` over the `count` threads of named barrier `id` (a barrier too)
+__device__ __forceinline__ bool bar_and(int id, int count, bool pred) {
+  unsigned r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+      "barrier.cta.red.and.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((unsigned)pred), "r"(id), "r"(count)
+      : "memory");
+  return r != 0;
+}
+
 // Optional index checks (build with -DPSC_CHECKED=1): an out-of-range global
 // index is not accessed; bit 0 of Ctrl::err is raised instead.
 #ifndef PSC_CHECKED

@@ -19,6 +19,7 @@ struct CombineArgs {
   const void* ep;     // exp(-D k^2 dt/2)
   Ctrl* ctrl;
   double kF2, beta, nu, D;
+  int kF2_floor;  // floor(kF2): the band test in integers
   int forcing, integrator, scalar_on;
 };
 
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(256) k_combine(CombineArgs c) {
   }
   // the stage input is needed in full only on the forcing band and for the
   // explicit linear terms of plain RK4; elsewhere only u2 (scalar source)
-  const bool band = c.forcing && k2 > 0 && (double)k2 <= c.kF2;
+  const bool band = c.forcing && k2 > 0 && k2 <= c.kF2_floor;
   const bool all = band || c.integrator == 1;
   const C zero = mk(T(0), T(0));
   const C v1 = vin[S + i];

@@ -465,10 +465,8 @@ k_xpass(PassArgs a) {
   const long long nlines = (long long)N * N;
   const T scale = T(1.0 / ((double)N * N * N));
   const C zero = mk(T(0), T(0));
-  double umax = 0.0;
-  double acc[NQ];
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+  T um = T(0);  // maximum of |u1|+|u2|+|u3| over the thread's points
+  MomentSum<T> acc[MODE == XMODE_STATS ? NQ : 1];
 
 #pragma unroll 1
   for (long long grp = (long long)blockIdx.x * XC::WARPS + wid; grp * LPW < nlines;
@@ -516,10 +514,7 @@ k_xpass(PassArgs a) {
           else uz[j][k2] = u3;
           nly[j][k2] = u3 * w1;
           nlz[j][k2] = -getu(1, j, k2) * w1;
-          if (a.want_umax) {
-            const double s3 = (double)(fabs(getu(0, j, k2)) + fabs(getu(1, j, k2)) + fabs(u3));
-            umax = s3 > umax || s3 != s3 ? s3 : umax;
-          }
+          if (a.want_umax) um = max_keep_nan(um, fabs(getu(0, j, k2)) + fabs(getu(1, j, k2)) + fabs(u3));
         }
       // (omega_2, omega_3):  omega_2 = d_z u_1 - i kx u_3,  omega_3 = i kx u_2 - d_y u_1
       xinv<T, N>(
@@ -589,9 +584,9 @@ k_xpass(PassArgs a) {
       (void)mom;
       auto acc234 = [&](int q, int j, int k2, T v) {
         const T v2 = v * v;
-        acc[q] += (double)v2;
-        acc[q + 1] += (double)(v2 * v);
-        acc[q + 2] += (double)(v2 * v2);
+        acc[q].add(v2);
+        acc[q + 1].add(v2 * v);
+        acc[q + 2].add(v2 * v2);
         (void)j; (void)k2;
       };
       // (u1, u3)
@@ -601,7 +596,7 @@ k_xpass(PassArgs a) {
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) {
           const T u1 = z[j][k2].x, u3 = z[j][k2].y;
-          acc[0] += (double)(u1 * u1 + u3 * u3);
+          acc[0].add(u1 * u1 + u3 * u3);
           s13[j][k2] = fabs(u1) + fabs(u3);
         }
       // (u2, phi)
@@ -611,11 +606,10 @@ k_xpass(PassArgs a) {
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) {
           const T u2 = z[j][k2].x, ph = z[j][k2].y;
-          acc[0] += (double)(u2 * u2);
-          acc[20] += (double)(ph * u2);
-          acc[21] += (double)(ph * ph);
-          const double s3 = (double)(s13[j][k2] + fabs(u2));
-          umax = s3 > umax || s3 != s3 ? s3 : umax;
+          acc[0].add(u2 * u2);
+          acc[20].add(ph * u2);
+          acc[21].add(ph * ph);
+          um = max_keep_nan(um, s13[j][k2] + fabs(u2));
         }
       // (omega_1, omega_2)
       xinv<T, N>(
@@ -628,7 +622,7 @@ k_xpass(PassArgs a) {
       for (int j = 0; j < J2; ++j)
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2)
-          acc[1] += (double)(z[j][k2].x * z[j][k2].x + z[j][k2].y * z[j][k2].y);
+          acc[1].add(z[j][k2].x * z[j][k2].x + z[j][k2].y * z[j][k2].y);
       // (omega_3, dphi/dx1)
       xinv<T, N>(
           [&](int kx, C& x1, C& x2) {
@@ -640,7 +634,7 @@ k_xpass(PassArgs a) {
       for (int j = 0; j < J2; ++j)
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) {
-          acc[1] += (double)(z[j][k2].x * z[j][k2].x);
+          acc[1].add(z[j][k2].x * z[j][k2].x);
           acc234(11, j, k2, z[j][k2].y);
         }
       // (dphi/dx2, dphi/dx3)
@@ -673,6 +667,7 @@ k_xpass(PassArgs a) {
   }
 
   if (MODE == XMODE_STATS || a.want_umax) {
+    double umax = (double)um;  // the fields here are scaled
     for (int o = 16; o > 0; o >>= 1) {
       const double other = __shfl_xor_sync(0xffffffffu, umax, o);
       umax = other > umax || other != other ? other : umax;
@@ -683,7 +678,7 @@ k_xpass(PassArgs a) {
     const long long gw = (long long)blockIdx.x * XC::WARPS + wid;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-      double v = acc[q];
+      double v = acc[q].value();
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       if (lane == 0) a.partials[gw * NQ + q] = v;
     }
@@ -757,7 +752,34 @@ template <typename T, int N> struct Passes {
   static void yinv(const PassArgs& a, bool stats, int v) { v ? yinv_w<WV1>(a, stats) : yinv_w<WV0>(a, stats); }
   static void yfwd(const PassArgs& a, int v) { v ? yfwd_w<WV1>(a) : yfwd_w<WV0>(a); }
   static void zfwd(const PassArgs& a, int v) { v ? zfwd_w<WV1>(a) : zfwd_w<WV0>(a); }
+  // the right-hand side at N = 1024 (FP32) stages its rows through shared memory
+#ifndef PSC_X2S
+#define PSC_X2S 1
+#endif
+  static constexpr bool X2S = PSC_X2S && X2 && N == 1024 && sizeof(T) == 4;
+  static int sm_count() {
+    static int n[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 152;
+    if (n[dev] == 0) {
+      int c = 0;
+      cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+      n[dev] = c > 0 ? c : 152;
+    }
+    return n[dev];
+  }
   static void xpass(const PassArgs& a, int mode) {
+    if constexpr (X2S) {
+      if (mode == XMODE_RHS) {
+        using SC = X2SCfg<T, N>;
+        const long long rows = (long long)N * N / SC::ROWS;
+        const int grid = (int)(rows < sm_count() ? rows : sm_count());
+        prep(k_xpass2s<T, N>, SC::SMEM);
+        k_xpass2s<T, N><<<grid, SC::THREADS, SC::SMEM, a.st>>>(a);
+        return;
+      }
+    }
     if constexpr (X2) {
       const size_t sm2 = X2Cfg<T, N>::SMEM;
       if (mode == XMODE_STATS) {

@@ -206,6 +206,100 @@ __device__ __forceinline__ void x2fwd(typename CT<T>::type (&z)[16], const OUT& 
   row_sync<TH>(q.bar);
 }
 
+// Fill the per-role twiddle tables T1, T3, T2 (see X2Cfg) at `t1` and point
+// the roles at them; ends with a CTA barrier.
+template <typename T, int N>
+__device__ __forceinline__ void x2_twiddles(typename CT<T>::type* t1, const typename CT<T>::type* __restrict__ tw,
+                                            X2Roles<typename CT<T>::type>& q) {
+  using C = typename CT<T>::type;
+  constexpr int TH = X2Cfg<T, N>::TH, G = X2Cfg<T, N>::G;
+  C* t3 = t1 + 16 * TH;
+  C* t2 = t3 + 16 * TH;
+  for (int i = threadIdx.x; i < 16 * TH; i += blockDim.x) {
+    const int e = i / TH, tid = i % TH;  // e = a for T1, k1 for T3
+    const int ra = tid / G, rk0 = bitrev_lane<G>(tid % G);
+    t1[i] = tw[e * tid];
+    t3[i] = tw[ra * (rk0 + G * e)];
+  }
+  for (int i = threadIdx.x; i < 16 * G; i += blockDim.x) t2[i] = tw[16 * (i / G) * (i % G)];
+  q.t1 = t1;
+  q.t2 = t2;
+  q.t3 = t3;
+  __syncthreads();
+}
+
+// Right-hand side of one row (z, y): five inverse transforms of packed field
+// pairs, u x omega and u . grad phi in registers, two forward transforms.
+// Y(s, kx) reads stream s at kx.  after_a() runs once streams UX..DYUX are no
+// longer read, wait_b() before PHI..DZPHI are first read (false aborts the
+// row), after_b() once those are no longer read.  Returns false if aborted.
+template <typename T, int N, class YF, class HA, class WB, class HB>
+__device__ __forceinline__ bool x2_rhs_row(const YF& Y, const HA& after_a, const WB& wait_b, const HB& after_b,
+                                           typename CT<T>::type* __restrict__ xb, long long line, long long ys,
+                                           typename CT<T>::type* ex, const X2Roles<typename CT<T>::type>& q,
+                                           T scale, bool want_umax, T& um, Ctrl* ctrl) {
+  using C = typename CT<T>::type;
+  constexpr int M = X2Cfg<T, N>::K + 1;
+  const C zero = mk(T(0), T(0));
+  (void)ctrl;
+  C z[16];
+  // the inverse transforms are left unscaled (N^3 times the fields); each
+  // product carries the missing 1/N^6 once
+  const T s2 = scale * scale;
+  // live per thread at most: u1, u2, u3 and one more field (64 values)
+  T u1[16], u2[16], u3[16], W[16];
+  // (u1, u2)
+  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UY, kx); }, z, ex, q, scale);
+#pragma unroll
+  for (int b = 0; b < 16; ++b) { u1[b] = z[b].x; u2[b] = z[b].y; }
+  // (u3, omega1)
+  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UZ, kx); x2 = Y(Y_WX, kx); }, z, ex, q, scale);
+#pragma unroll
+  for (int b = 0; b < 16; ++b) {
+    u3[b] = z[b].x;
+    W[b] = z[b].y;  // omega1
+    if (want_umax) um = max_keep_nan(um, fabs(u1[b]) + fabs(u2[b]) + fabs(u3[b]));
+  }
+  // (omega2, omega3): omega2 = d_z u1 - i kx u3, omega3 = i kx u2 - d_y u1
+  x2inv<T, N, false>(
+      [&](int kx, C& x1, C& x2) {
+        x1 = csub(Y(Y_DZUX, kx), mul_ik(Y(Y_UZ, kx), T(kx)));
+        x2 = csub(mul_ik(Y(Y_UY, kx), T(kx)), Y(Y_DYUX, kx));
+      },
+      z, ex, q, scale);
+  after_a();
+#pragma unroll
+  for (int b = 0; b < 16; ++b) {
+    const T w1 = W[b], w2 = z[b].x, w3 = z[b].y;
+    z[b] = mk((u2[b] * w3 - u3[b] * w2) * s2, (u3[b] * w1 - u1[b] * w3) * s2);  // (NL1, NL2)
+    W[b] = u1[b] * w2 - u2[b] * w1;                                              // NL3
+  }
+  x2fwd<T, N>(z,
+              [&](int kx, C X1, C X2) {
+                const long long i0 = line * M + kx;
+                if (PSC_OK_INDEX(i0 + ys, 4 * ys, ctrl)) { xb[i0] = X1; xb[i0 + ys] = X2; }
+              },
+              ex, q);
+  if (!wait_b()) return false;
+  // (dphi/dx1, dphi/dx2); u1 then holds the partial u . grad phi
+  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_PHI, kx), T(kx)); x2 = Y(Y_DYPHI, kx); },
+                     z, ex, q, scale);
+#pragma unroll
+  for (int b = 0; b < 16; ++b) u1[b] = u1[b] * z[b].x + u2[b] * z[b].y;
+  // (dphi/dx3, 0)
+  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZPHI, kx); x2 = zero; }, z, ex, q, scale);
+  after_b();
+#pragma unroll
+  for (int b = 0; b < 16; ++b) z[b] = mk(W[b] * s2, (u1[b] + u3[b] * z[b].x) * s2);  // (NL3, u.grad phi)
+  x2fwd<T, N>(z,
+              [&](int kx, C X1, C X2) {
+                const long long i0 = 2 * ys + line * M + kx;
+                if (PSC_OK_INDEX(i0 + ys, 4 * ys, ctrl)) { xb[i0] = X1; xb[i0 + ys] = X2; }
+              },
+              ex, q);
+  return true;
+}
+
 template <typename T>
 __device__ __forceinline__ double warp_sum_d(T v) {
   double d = (double)v;
@@ -235,30 +329,15 @@ __global__ void __launch_bounds__(128, PSC_X2_MINB) k_xpass2(PassArgs a) {
   const C* __restrict__ yb = static_cast<const C*>(a.yb);
   C* __restrict__ xb = static_cast<C*>(a.xb);
   const C* __restrict__ tw = static_cast<const C*>(a.tw);
-  {
-    C* t1 = reinterpret_cast<C*>(smraw + XC::LINE_BYTES * ROWS + XC::ACC_BYTES);
-    C* t3 = t1 + 16 * TH;
-    C* t2 = t3 + 16 * TH;
-    for (int i = threadIdx.x; i < 16 * TH; i += blockDim.x) {
-      const int e = i / TH, tid = i % TH;  // e = a for T1, k1 for T3
-      const int ra = tid / G, rk0 = bitrev_lane<G>(tid % G);
-      t1[i] = tw[e * tid];
-      t3[i] = tw[ra * (rk0 + G * e)];
-    }
-    for (int i = threadIdx.x; i < 16 * G; i += blockDim.x) t2[i] = tw[16 * (i / G) * (i % G)];
-    q.t1 = t1;
-    q.t2 = t2;
-    q.t3 = t3;
-    __syncthreads();
-  }
+  x2_twiddles<T, N>(reinterpret_cast<C*>(smraw + XC::LINE_BYTES * ROWS + XC::ACC_BYTES), tw, q);
   const long long ys = (long long)N * N * M;
   const long long nlines = (long long)N * N;
   const T scale = T(1.0 / ((double)N * N * N));
   const C zero = mk(T(0), T(0));
-  double umax = 0.0;
-  double acc[MODE == XMODE_STATS ? NQ : 1];
-#pragma unroll
-  for (int i = 0; i < (MODE == XMODE_STATS ? NQ : 1); ++i) acc[i] = 0.0;
+  // maximum of |u1|+|u2|+|u3| over the thread's points (unscaled fields in the
+  // RHS variant, scaled in the statistics variant)
+  T um = T(0);
+  MomentSum<T> acc[MODE == XMODE_STATS ? NQ : 1];
 
 #pragma unroll 1
   for (long long base = (long long)blockIdx.x * ROWS; base < nlines; base += (long long)gridDim.x * ROWS) {
@@ -270,66 +349,14 @@ __global__ void __launch_bounds__(128, PSC_X2_MINB) k_xpass2(PassArgs a) {
     };
     C z[16];
     if constexpr (MODE == XMODE_RHS) {
-      // the inverse transforms are left unscaled (N^3 times the fields); each
-      // product carries the missing 1/N^6 once
-      const T s2 = scale * scale;
-      T u1[16], u2[16], u3[16], A1[16], A2[16];
-      // (u1, u2)
-      x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UY, kx); }, z, ex, q, scale);
-#pragma unroll
-      for (int b = 0; b < 16; ++b) { u1[b] = z[b].x; u2[b] = z[b].y; }
-      // (u3, omega1)
-      x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UZ, kx); x2 = Y(Y_WX, kx); }, z, ex, q, scale);
-#pragma unroll
-      for (int b = 0; b < 16; ++b) {
-        u3[b] = z[b].x;
-        A1[b] = z[b].x * z[b].y;    // u3 omega1 (part of NL2)
-        A2[b] = -u2[b] * z[b].y;    // -u2 omega1 (part of NL3)
-        if (a.want_umax) {
-          const double s3 = (double)(fabs(u1[b]) + fabs(u2[b]) + fabs(u3[b])) * (double)scale;
-          umax = s3 > umax || s3 != s3 ? s3 : umax;
-        }
-      }
-      // (omega2, omega3): omega2 = d_z u1 - i kx u3, omega3 = i kx u2 - d_y u1
-      x2inv<T, N, false>(
-          [&](int kx, C& x1, C& x2) {
-            x1 = csub(Y(Y_DZUX, kx), mul_ik(Y(Y_UZ, kx), T(kx)));
-            x2 = csub(mul_ik(Y(Y_UY, kx), T(kx)), Y(Y_DYUX, kx));
-          },
-          z, ex, q, scale);
-#pragma unroll
-      for (int b = 0; b < 16; ++b) {
-        const T w2 = z[b].x, w3 = z[b].y;
-        z[b] = mk((u2[b] * w3 - u3[b] * w2) * s2, (A1[b] - u1[b] * w3) * s2);  // (NL1, NL2)
-        A2[b] += u1[b] * w2;                                     // NL3
-      }
-      x2fwd<T, N>(z,
-                  [&](int kx, C X1, C X2) {
-                    const long long i0 = line * M + kx;
-                    if (PSC_OK_INDEX(i0 + ys, 4 * ys, a.ctrl)) { xb[i0] = X1; xb[i0 + ys] = X2; }
-                  },
-                  ex, q);
-      // (dphi/dx1, dphi/dx2)
-      x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_PHI, kx), T(kx)); x2 = Y(Y_DYPHI, kx); },
-                  z, ex, q, scale);
-#pragma unroll
-      for (int b = 0; b < 16; ++b) A1[b] = u1[b] * z[b].x + u2[b] * z[b].y;
-      // (dphi/dx3, 0)
-      x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZPHI, kx); x2 = zero; }, z, ex, q, scale);
-#pragma unroll
-      for (int b = 0; b < 16; ++b) z[b] = mk(A2[b] * s2, (A1[b] + u3[b] * z[b].x) * s2);  // (NL3, u.grad phi)
-      x2fwd<T, N>(z,
-                  [&](int kx, C X1, C X2) {
-                    const long long i0 = 2 * ys + line * M + kx;
-                    if (PSC_OK_INDEX(i0 + ys, 4 * ys, a.ctrl)) { xb[i0] = X1; xb[i0 + ys] = X2; }
-                  },
-                  ex, q);
+      x2_rhs_row<T, N>(Y, [] {}, [] { return true; }, [] {}, xb, line, ys, ex, q, scale, a.want_umax != 0,
+                       um, a.ctrl);
     } else {
       // statistics (Eqs. 11-13): per pair, partial sums of the thread's 16
       // points, added in FP64 to the thread's accumulators (reduced over the
       // warp once, at the end)
       T s13[16];
-      auto put = [&](int slot, T v) { acc[slot] += (double)v; };
+      auto put = [&](int slot, T v) { acc[slot].add(v); };
       auto mom3 = [&](int slot, const T (&f)[16]) {
         T m2 = T(0), m3 = T(0), m4 = T(0);
 #pragma unroll
@@ -358,8 +385,7 @@ __global__ void __launch_bounds__(128, PSC_X2_MINB) k_xpass2(PassArgs a) {
 #pragma unroll
         for (int b = 0; b < 16; ++b) {
           s0 += f1[b] * f1[b]; s1 += f2[b] * f1[b]; s2 += f2[b] * f2[b];
-          const double s3 = (double)(s13[b] + fabs(f1[b]));
-          umax = s3 > umax || s3 != s3 ? s3 : umax;
+          um = max_keep_nan(um, s13[b] + fabs(f1[b]));
         }
         put(0, s0); put(20, s1); put(21, s2);
       }
@@ -408,6 +434,9 @@ __global__ void __launch_bounds__(128, PSC_X2_MINB) k_xpass2(PassArgs a) {
   }
 
   if (MODE == XMODE_STATS || a.want_umax) {
+    // the same value as taking the FP64 maximum point by point: conversion and
+    // the positive scaling are monotone
+    double umax = MODE == XMODE_STATS ? (double)um : (double)um * (double)scale;
     for (int o = 16; o > 0; o >>= 1) {
       const double other = __shfl_xor_sync(0xffffffffu, umax, o);
       umax = other > umax || other != other ? other : umax;
@@ -418,11 +447,147 @@ __global__ void __launch_bounds__(128, PSC_X2_MINB) k_xpass2(PassArgs a) {
     const long long gw = (long long)blockIdx.x * 4 + wid;
 #pragma unroll
     for (int i = 0; i < NQ; ++i) {
-      const double v = warp_sum_d<double>(acc[i]);
+      const double v = warp_sum_d<double>(acc[i].value());
       if (lane == 0) a.partials[gw * NQ + i] = v;
     }
   }
   (void)accw;
+}
+
+// ---------------------------------------------------------------------------
+// Staged x pass (right-hand side, FP32, N = 1024).  One CTA per SM holds
+// X2SCfg::ROWS rows in flight; the nine input streams of each row are copied
+// into shared memory by bulk asynchronous copies (TMA engine) one row ahead,
+// in two groups completed on two mbarriers: UX..DYUX (read by the first three
+// inverse transforms) and PHI..DZPHI (read by the last two).  Each group of the
+// next row is issued as soon as the current row stops reading it, so global
+// latency overlaps at least three transforms, and the transforms read their
+// inputs from shared memory.
+// ---------------------------------------------------------------------------
+template <typename T, int N> struct X2SCfg {
+  using C = typename CT<T>::type;
+  using XC = X2Cfg<T, N>;
+#ifndef PSC_X2S_ROWS
+#define PSC_X2S_ROWS 6
+#endif
+  static constexpr int ROWS = PSC_X2S_ROWS;
+  static constexpr int THREADS = XC::TH * ROWS;
+  static constexpr int M = XC::K + 1;
+  static constexpr int NA = 6, NB = 3;  // streams Y_UX..Y_DYUX, Y_PHI..Y_DZPHI
+  static constexpr unsigned ROW_BYTES = (unsigned)(M * sizeof(C));
+  static constexpr size_t STAGE_BYTES = (size_t)(NA + NB) * ROW_BYTES;
+  static constexpr size_t GROUP_BYTES = STAGE_BYTES + XC::LINE_BYTES;
+  static constexpr size_t TW_OFF = GROUP_BYTES * ROWS;
+  static constexpr size_t BAR_OFF = TW_OFF + XC::TW_BYTES;
+  static constexpr size_t SMEM = BAR_OFF + 2 * ROWS * sizeof(unsigned long long);
+  static constexpr bool OK = ROW_BYTES % 16 == 0 && SMEM <= 227 * 1024;
+  static_assert(Y_UX == 0 && Y_DYUX == NA - 1 && Y_PHI == NA && Y_DZPHI == NA + NB - 1,
+                "staged streams are contiguous");
+};
+
+template <typename T, int N>
+__global__ void __launch_bounds__(X2SCfg<T, N>::THREADS, 1) k_xpass2s(PassArgs a) {
+  using C = typename CT<T>::type;
+  using XC = X2Cfg<T, N>;
+  using SC = X2SCfg<T, N>;
+  static_assert(SC::OK, "staged x pass: rows must be 16-byte multiples and fit shared memory");
+  constexpr int TH = XC::TH, G = XC::G, ROWS = SC::ROWS, M = SC::M;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int lid = threadIdx.x / TH;
+  X2Roles<C> q;
+  q.tid = threadIdx.x % TH;
+  q.ra = q.tid / G;
+  q.rr = q.tid % G;
+  q.rk0 = bitrev_lane<G>(q.rr);
+  q.bar = 1 + lid;
+  unsigned char* grp = smraw + (size_t)lid * SC::GROUP_BYTES;
+  C* stg = reinterpret_cast<C*>(grp);
+  C* ex = reinterpret_cast<C*>(grp + SC::STAGE_BYTES);
+  unsigned long long* barA = reinterpret_cast<unsigned long long*>(smraw + SC::BAR_OFF) + 2 * lid;
+  unsigned long long* barB = barA + 1;
+  const C* __restrict__ yb = static_cast<const C*>(a.yb);
+  C* __restrict__ xb = static_cast<C*>(a.xb);
+  if (q.tid == 0) {
+    mbar_init(barA, 1);
+    mbar_init(barB, 1);
+    mbar_init_fence();
+  }
+  x2_twiddles<T, N>(reinterpret_cast<C*>(smraw + SC::TW_OFF), static_cast<const C*>(a.tw), q);
+  const long long ys = (long long)N * N * M;
+  const long long nlines = (long long)N * N;
+  const long long stride = (long long)gridDim.x * ROWS;
+  const T scale = T(1.0 / ((double)N * N * N));
+  const bool leader = q.tid == 0;
+  // copies of streams [s0, s1) of row ln into the staging slots (one thread)
+  auto issue = [&](long long ln, int s0, int s1, unsigned long long* bar) {
+    fence_proxy_async_smem();
+    mbar_expect_tx(bar, (unsigned)(s1 - s0) * SC::ROW_BYTES);
+    for (int st = s0; st < s1; ++st) {
+      const long long src = st * ys + ln * M;
+      if (PSC_OK_INDEX(src + M - 1, (long long)Y_NSTREAM * ys, a.ctrl))
+        bulk_copy_g2s(stg + st * M, yb + src, SC::ROW_BYTES, bar);
+    }
+  };
+  T um = T(0);
+  unsigned pa = 0, pb = 0;        // parity of the next phase to wait for
+  bool ia = false, ib = false;    // a group issued and not yet waited for
+  bool ok = true;
+  long long line = (long long)blockIdx.x * ROWS + lid;
+  if (line < nlines) {
+    if (leader) {
+      issue(line, 0, SC::NA, barA);
+      issue(line, SC::NA, SC::NA + SC::NB, barB);
+    }
+    ia = ib = true;
+  }
+#pragma unroll 1
+  for (; line < nlines; line += stride) {
+    const long long next = line + stride;
+    ok = bar_and(q.bar, TH, mbar_wait(barA, pa));
+    if (!ok) break;
+    pa ^= 1u;
+    ia = false;
+    auto Y = [&](int st, int kx) -> C { return stg[st * M + kx]; };
+    ok = x2_rhs_row<T, N>(
+        Y,
+        [&] {
+          if (next < nlines) {
+            if (leader) issue(next, 0, SC::NA, barA);
+            ia = true;
+          }
+        },
+        [&] {
+          const bool w = bar_and(q.bar, TH, mbar_wait(barB, pb));
+          if (w) {
+            pb ^= 1u;
+            ib = false;
+          }
+          return w;
+        },
+        [&] {
+          if (next < nlines) {
+            if (leader) issue(next, SC::NA, SC::NA + SC::NB, barB);
+            ib = true;
+          }
+        },
+        xb, line, ys, ex, q, scale, a.want_umax != 0, um, a.ctrl);
+    if (!ok) break;
+  }
+  if (!ok) {
+    // a copy did not complete in time: report it, give copies still in flight
+    // a bounded time to land in this CTA's shared memory, and stop
+    if (leader) atomicOr(&a.ctrl->err, 4);
+    if (ia) mbar_wait(barA, pa);
+    if (ib) mbar_wait(barB, pb);
+  }
+  if (a.want_umax) {
+    double umax = (double)um * (double)scale;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double other = __shfl_xor_sync(0xffffffffu, umax, o);
+      umax = other > umax || other != other ? other : umax;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(&a.ctrl->umax_bits, (unsigned long long)__double_as_longlong(umax));
+  }
 }
 
 }  // namespace psc
