@@ -467,7 +467,7 @@ def main():
            "step_roofline": {"algorithmic_bytes_per_step": step_bytes,
                              "achieved_GBps": round(step_bytes / (ms / a.steps / 1000.0) / 1e9, 1),
                              "frac": round(step_bytes / (ms / a.steps / 1000.0) / 1e9 / peak, 4)},
-           "kernels": per_kernel, "tile_widths": sim.tile_widths(), "gpu_launches": launches,
+           "kernels": per_kernel, "tile_widths": sim.tile_widths(), "tile_staged": sim.tile_staged(), "gpu_launches": launches,
            "clocks": clk.summary(),
            "last_record": {k: last_rec[k] for k in ("t", "dt", "K", "eps", "Re_lambda", "kmax_eta", "cfl",
                                                     "phi_var", "chi")}}

@@ -189,6 +189,12 @@ psc_status psc_profile_read(psc_sim* s, double* ms, int64_t* launches, int32_t n
  * fixed defaults instead). */
 psc_status psc_tile_widths(const psc_sim* s, int32_t* w);
 
+/* Whether each of the four strided passes (same order as psc_tile_widths)
+ * runs its TMA-staged kernel: 1 if the pass brings its input tiles into shared
+ * memory with bulk tensor copies ahead of each transform, 0 if its threads
+ * load from global memory directly.  Chosen by the same autotuning. */
+psc_status psc_tile_staged(const psc_sim* s, int32_t* staged);
+
 /* Total kernels this simulation has launched since creation (always counted). */
 psc_status psc_launch_count(const psc_sim* s, int64_t* n);
 

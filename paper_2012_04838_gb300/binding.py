@@ -75,6 +75,7 @@ EXPORTS = [
     ("psc_profile_read", ct.c_int, [_VP, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.c_int32]),
     ("psc_launch_count", ct.c_int, [_VP, ct.POINTER(ct.c_int64)]),
     ("psc_tile_widths", ct.c_int, [_VP, ct.POINTER(ct.c_int32)]),
+    ("psc_tile_staged", ct.c_int, [_VP, ct.POINTER(ct.c_int32)]),
     ("psc_destroy", ct.c_int, [_VP]),
     ("psc_shell_spectra_noalloc", ct.c_int, [_VP, ct.c_int32, ct.c_int32, ct.POINTER(ct.c_double),
                                              ct.POINTER(ct.c_double), ct.c_int32, _VP]),
@@ -263,6 +264,12 @@ class Simulation:
         w = (ct.c_int32 * 4)()
         _check(self.lib, self.lib.psc_tile_widths(self._h, w))
         return dict(zip(("zinv", "yinv", "yfwd", "zfwd"), list(w)))
+
+    def tile_staged(self) -> dict:
+        """{pass: True if it stages input tiles through shared memory by TMA}."""
+        w = (ct.c_int32 * 4)()
+        _check(self.lib, self.lib.psc_tile_staged(self._h, w))
+        return dict(zip(("zinv", "yinv", "yfwd", "zfwd"), [bool(v) for v in w]))
 
     def launch_count(self) -> int:
         n = ct.c_int64()

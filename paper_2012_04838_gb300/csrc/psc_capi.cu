@@ -335,6 +335,12 @@ psc_status psc_tile_widths(const psc_sim* s, int32_t* w) {
   return PSC_OK;
 }
 
+psc_status psc_tile_staged(const psc_sim* s, int32_t* staged) {
+  if (!s || !staged) return fail(PSC_EINVAL, "null argument");
+  for (int p = 0; p < SP_N; ++p) staged[p] = s->tb->staged[s->wv[p]];
+  return PSC_OK;
+}
+
 psc_status psc_launch_count(const psc_sim* s, int64_t* n) {
   if (!s || !n) return fail(PSC_EINVAL, "null argument");
   *n = s->launches;
@@ -594,9 +600,10 @@ psc_status do_stats(psc_sim* s, double* Ek, double* Ephi, int cap, int* nshell, 
   return PSC_OK;
 }
 
-// Tile-width autotuner of the strided passes.  Both compiled widths of each
-// pass are timed on this simulation's own workspace (one warm-up and three
-// timed launches each, CUDA events on its stream) and the faster is kept.
+// Autotuner of the strided passes.  Every compiled variant of each pass (tile
+// widths, and for FP32 grids with an even M the TMA-staged kernels) is timed
+// on this simulation's own workspace (one warm-up and three timed launches
+// each, CUDA events on its stream) and the fastest is kept.
 // Choices are cached per (grid size, precision) for the life of the process,
 // so ensembles and servers tune once per N.  PSC_TUNE=0 in the environment
 // skips the timing and uses 128-byte runs (16 columns) for the z passes and for
@@ -613,6 +620,20 @@ psc_status autotune(psc_sim* s) {
   s->wv[SP_ZFWD] = 1;
   s->wv[SP_YINV] = ypass_narrow ? 0 : 1;
   s->wv[SP_YFWD] = ypass_narrow ? 0 : 1;
+  // PSC_STRIDED_VARIANT=v runs variant v of every strided pass; four digits
+  // give the z-inverse, y-inverse, y-forward and z-forward variants (tests)
+  const char* force = std::getenv("PSC_STRIDED_VARIANT");
+  if (force && force[0] >= '0' && force[0] <= '9') {
+    const size_t len = std::strlen(force);
+    for (int p = 0; p < SP_N; ++p) {
+      const char c = len == (size_t)SP_N ? force[p] : force[0];
+      const int v = c - '0';
+      if (len != 1 && len != (size_t)SP_N) return fail(PSC_EINVAL, "PSC_STRIDED_VARIANT: one or four digits");
+      if (v < 0 || v >= s->tb->nvariants) return fail(PSC_EINVAL, "PSC_STRIDED_VARIANT out of range for this grid");
+      s->wv[p] = v;
+    }
+    return PSC_OK;
+  }
   const char* env = std::getenv("PSC_TUNE");
   if (env && env[0] == '0') return PSC_OK;
   const std::pair<int, int> key(N, s->fp64);
@@ -641,7 +662,7 @@ psc_status autotune(psc_sim* s) {
   for (int p = 0; p < SP_N && e == cudaSuccess; ++p) {
     float tbest = 0.f;
     best[p] = s->wv[p];
-    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+    for (int v = 0; v < s->tb->nvariants && e == cudaSuccess; ++v) {
       run(p, v);
       cudaEventRecord(e0, s->st);
       for (int r = 0; r < 3; ++r) run(p, v);

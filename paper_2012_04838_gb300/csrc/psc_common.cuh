@@ -26,9 +26,14 @@ template <class C> __device__ __forceinline__ C cmul(C a, C b) {
 template <class C> __device__ __forceinline__ C cmulc(C a, C b) {
   return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
-// i * k * a
-template <class C, typename T> __device__ __forceinline__ C mul_ik(C a, T k) {
-  return mk(-k * a.y, k * a.x);
+// i * k * a.  The products are rounded on their own (never fused into a
+// following addition), so every kernel variant that forms a derivative this
+// way produces the same bits whatever the compiler contracts around it.
+__device__ __forceinline__ float2 mul_ik(float2 a, float k) {
+  return make_float2(__fmul_rn(-k, a.y), __fmul_rn(k, a.x));
+}
+__device__ __forceinline__ double2 mul_ik(double2 a, double k) {
+  return make_double2(__dmul_rn(-k, a.y), __dmul_rn(k, a.x));
 }
 template <class C> __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
 template <class C> __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }

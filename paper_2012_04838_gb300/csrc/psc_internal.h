@@ -80,8 +80,9 @@ struct PassTable {
   void (*yfwd)(const PassArgs&, int v);
   void (*zfwd)(const PassArgs&, int v);
   int xwarps;       // warps launched by the X pass (rows of `partials`)
-  int nvariants;    // tile-width variants of the strided passes (1 or 2)
-  int widths[2];    // their column tile widths
+  int nvariants;    // variants of the strided passes (1, 2 or 4)
+  int widths[4];    // their column tile widths
+  int staged[4];    // 1: input tiles staged through shared memory by TMA
 };
 
 const PassTable* table_f32(int N);

@@ -688,6 +688,7 @@ k_xpass(PassArgs a) {
 }  // namespace psc
 
 #include "psc_xpass2.cuh"
+#include "psc_staged.cuh"
 
 namespace psc {
 
@@ -748,10 +749,66 @@ template <typename T, int N> struct Passes {
     prep(k_zfwd<T, N, W>, sm);
     k_zfwd<T, N, W><<<grid, block, sm, a.st>>>(a);
   }
-  static void zinv(const PassArgs& a, bool stats, int v) { v ? zinv_w<WV1>(a, stats) : zinv_w<WV0>(a, stats); }
-  static void yinv(const PassArgs& a, bool stats, int v) { v ? yinv_w<WV1>(a, stats) : yinv_w<WV0>(a, stats); }
-  static void yfwd(const PassArgs& a, int v) { v ? yfwd_w<WV1>(a) : yfwd_w<WV0>(a); }
-  static void zfwd(const PassArgs& a, int v) { v ? zfwd_w<WV1>(a) : zfwd_w<WV0>(a); }
+  // variants 2 and 3: input tiles staged by TMA, 4 and 8 columns (FP32, M even)
+#ifndef PSC_STAGED
+#define PSC_STAGED 1
+#endif
+  static constexpr bool STAGED = PSC_STAGED && sizeof(T) == 4 && N >= 64 && M % 2 == 0;
+  static constexpr int NV = STAGED ? 4 : (WV0 != WV1 ? 2 : 1);
+  template <int W, int PASS, bool STATS> static bool launch_s(const PassArgs& a) {
+    if constexpr (STAGED) {
+      using TL = StagedTile<T, N, W, PASS == SP_ZINV || PASS == SP_YINV>;
+      CUtensorMap m;
+      bool ok;
+      int rows;
+      if constexpr (PASS == SP_ZINV) {
+        ok = make_row_map(&m, a.in, 3, M, P, 4LL * P, (long long)P * M, W, TL::BOXR);
+        rows = P;
+      } else if constexpr (PASS == SP_YINV) {
+        ok = make_row_map(&m, a.zb, 2, M, (long long)Z_NSTREAM * N * P, 0, 0, W, TL::BOXR);
+        rows = N;
+      } else if constexpr (PASS == SP_YFWD) {
+        ok = make_row_map(&m, a.xb, 2, M, 4LL * N * N, 0, 0, W, TL::BOXR);
+        rows = N;
+      } else {
+        ok = make_row_map(&m, a.yf, 3, M, P, 4LL * N, (long long)P * M, W, TL::BOXR);
+        rows = P;
+      }
+      if (!ok) return false;
+      prep(k_strided_s<T, N, W, PASS, STATS>, TL::SMEM);
+      k_strided_s<T, N, W, PASS, STATS><<<dim3((M + W - 1) / W, rows), dim3(W, TPL), TL::SMEM, a.st>>>(a, m);
+      return true;
+    } else {
+      (void)a;
+      return false;
+    }
+  }
+  template <int PASS> static bool staged(const PassArgs& a, bool stats, int v) {
+    if constexpr (PASS == SP_ZINV || PASS == SP_YINV) {
+      if (v == 2) return stats ? launch_s<4, PASS, true>(a) : launch_s<4, PASS, false>(a);
+      return stats ? launch_s<8, PASS, true>(a) : launch_s<8, PASS, false>(a);
+    } else {
+      (void)stats;
+      return v == 2 ? launch_s<4, PASS, false>(a) : launch_s<8, PASS, false>(a);
+    }
+  }
+  // a staged variant falls back to variant 0 if its tensor map cannot be made
+  static void zinv(const PassArgs& a, bool stats, int v) {
+    if (v >= 2 && staged<SP_ZINV>(a, stats, v)) return;
+    v == 1 ? zinv_w<WV1>(a, stats) : zinv_w<WV0>(a, stats);
+  }
+  static void yinv(const PassArgs& a, bool stats, int v) {
+    if (v >= 2 && staged<SP_YINV>(a, stats, v)) return;
+    v == 1 ? yinv_w<WV1>(a, stats) : yinv_w<WV0>(a, stats);
+  }
+  static void yfwd(const PassArgs& a, int v) {
+    if (v >= 2 && staged<SP_YFWD>(a, false, v)) return;
+    v == 1 ? yfwd_w<WV1>(a) : yfwd_w<WV0>(a);
+  }
+  static void zfwd(const PassArgs& a, int v) {
+    if (v >= 2 && staged<SP_ZFWD>(a, false, v)) return;
+    v == 1 ? zfwd_w<WV1>(a) : zfwd_w<WV0>(a);
+  }
   // the right-hand side at N = 1024 (FP32) stages its rows through shared memory
 #ifndef PSC_X2S
 #define PSC_X2S 1
@@ -803,8 +860,8 @@ template <typename T, int N> struct Passes {
   }
   static const PassTable* table() {
     static const PassTable tb = {&zinv, &yinv, &xpass, &yfwd, &zfwd,
-                                 xgrid() * (X2 ? 4 : XCfg<T, N>::WARPS), WV0 != WV1 ? 2 : 1,
-                                 {WV0, WV1}};
+                                 xgrid() * (X2 ? 4 : XCfg<T, N>::WARPS), NV,
+                                 {WV0, WV1, 4, 8}, {0, 0, 1, 1}};
     return &tb;
   }
 };
