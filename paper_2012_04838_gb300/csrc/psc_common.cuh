@@ -19,12 +19,17 @@ template <> struct CT<double> { typedef double2 type; };
 __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
 
+// Complex products with the fused multiply-add written out (one product
+// rounded, the other fused), so every kernel that multiplies by a twiddle
+// rounds the same way whatever the compiler would contract on its own.
+__device__ __forceinline__ float fmul_exact_order(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double fmul_exact_order(double a, double b) { return __dmul_rn(a, b); }
 template <class C> __device__ __forceinline__ C cmul(C a, C b) {
-  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  return mk(fma(a.x, b.x, -fmul_exact_order(a.y, b.y)), fma(a.x, b.y, fmul_exact_order(a.y, b.x)));
 }
 // a * conj(b)
 template <class C> __device__ __forceinline__ C cmulc(C a, C b) {
-  return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+  return mk(fma(a.x, b.x, fmul_exact_order(a.y, b.y)), fma(a.y, b.x, -fmul_exact_order(a.x, b.y)));
 }
 // i * k * a.  The products are rounded on their own (never fused into a
 // following addition), so every kernel variant that forms a derivative this

@@ -722,7 +722,10 @@ template <typename T, int N> struct Passes {
   }
 
   template <class KER> static void prep(KER k, size_t smem) {
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > 48 * 1024) {
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    }
   }
 
   template <int W> static void zinv_w(const PassArgs& a, bool stats) {

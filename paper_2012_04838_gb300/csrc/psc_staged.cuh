@@ -42,22 +42,24 @@ template <typename T, int N, int W, bool INV> struct StagedTile {
   static constexpr int BOXR = (((ROWS + NBOX - 1) / NBOX) + 1) & ~1;
   static constexpr unsigned BOX_BYTES = (unsigned)(BOXR * W * sizeof(C));
   static constexpr unsigned BYTES = NBOX * BOX_BYTES;
-  static constexpr size_t STG_OFF = (StridedSmem<T, N, W>::BYTES + 127) / 128 * 128;
+  // the exchange buffer, then the staging tile (twiddles are read through L1)
+  static constexpr size_t STG_OFF = (StridedSmem<T, N, W>::EXCH_BYTES + 127) / 128 * 128;
   static constexpr size_t BAR_OFF = STG_OFF + BYTES;
   static constexpr size_t SMEM = BAR_OFF + sizeof(unsigned long long);
-  // CTAs per SM that fit 227 KB of shared memory (1 KB reserved per CTA)
-  static constexpr int FIT = (int)((227 * 1024) / (SMEM + 1024));
+  // CTAs per SM that fit its 228 KB of shared memory (1 KB reserved per CTA)
+  static constexpr int FIT = (int)((228 * 1024) / (SMEM + 1024));
   static constexpr int MINB = FIT < 1 ? 1 : (FIT > 4 ? 4 : FIT);
   static_assert(BOX_BYTES % 128 == 0, "boxes start 128-byte aligned");
   static_assert(W * sizeof(C) % 16 == 0, "a box row is a multiple of 16 bytes");
 };
 
 // One length-N DFT per column from step-1 inputs already in registers:
-// in[j][n1] is line position R2 n1 + t + j TPL.  Same steps as strided_fft.
+// in[j][n1] is line position R2 n1 + t + j TPL.  Same steps as strided_fft,
+// with the step-1 twiddles wN^(n2 k1) read from the global table tw.
 template <typename T, int N, int W, int DIR, class ST>
 __device__ __forceinline__ void strided_fft_regs(typename CT<T>::type (&in)[PlanD<N>::J1][PlanD<N>::R1],
                                                  const ST& st, typename CT<T>::type* sm,
-                                                 const typename CT<T>::type* twsm, int t, int w) {
+                                                 const typename CT<T>::type* __restrict__ tw, int t, int w) {
   using C = typename CT<T>::type;
   using PL = PlanD<N>;
   using SM = StridedSmem<T, N, W>;
@@ -70,7 +72,7 @@ __device__ __forceinline__ void strided_fft_regs(typename CT<T>::type (&in)[Plan
     for (int k1 = 0; k1 < R1; ++k1) {
       C v = in[j][k1];
       if (k1 > 0) {
-        const C wv = twsm[(j * R1 + k1) * TPL + t];  // wN^(n2 k1)
+        const C wv = __ldg(&tw[n2 * k1]);  // wN^(n2 k1), n2 k1 < N
         v = (DIR < 0) ? cmul(v, wv) : cmulc(v, wv);
       }
       sm[k1 * SM::ROW + n2 * W + w] = v;
@@ -163,7 +165,8 @@ k_strided_s(PassArgs a, const __grid_constant__ CUtensorMap tm) {
     mbar_init(bar, 1);
     mbar_init_fence();
   }
-  const C* tw = strided_twiddles<T, N, W>(smraw, static_cast<const C*>(a.tw));  // ends with a barrier
+  const C* __restrict__ tw = static_cast<const C*>(a.tw);
+  __syncthreads();  // barrier initialised before any thread waits on it
   const long long S = (long long)P * P * M, zs = (long long)N * P * M, ys = (long long)N * N * M;
   auto issue = [&](int tr) {
     int src, kind, s2, out;
