@@ -629,7 +629,8 @@ psc_status autotune(psc_sim* s) {
       const char c = len == (size_t)SP_N ? force[p] : force[0];
       const int v = c - '0';
       if (len != 1 && len != (size_t)SP_N) return fail(PSC_EINVAL, "PSC_STRIDED_VARIANT: one or four digits");
-      if (v < 0 || v >= s->tb->nvariants) return fail(PSC_EINVAL, "PSC_STRIDED_VARIANT out of range for this grid");
+      if (v < 0 || v >= s->tb->nvariants || !((s->tb->vmask[p] >> v) & 1u))
+        return fail(PSC_EINVAL, "PSC_STRIDED_VARIANT: variant not built for this grid and pass");
       s->wv[p] = v;
     }
     return PSC_OK;
@@ -663,6 +664,7 @@ psc_status autotune(psc_sim* s) {
     float tbest = 0.f;
     best[p] = s->wv[p];
     for (int v = 0; v < s->tb->nvariants && e == cudaSuccess; ++v) {
+      if (!((s->tb->vmask[p] >> v) & 1u)) continue;
       run(p, v);
       cudaEventRecord(e0, s->st);
       for (int r = 0; r < 3; ++r) run(p, v);

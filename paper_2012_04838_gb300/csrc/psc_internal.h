@@ -80,9 +80,10 @@ struct PassTable {
   void (*yfwd)(const PassArgs&, int v);
   void (*zfwd)(const PassArgs&, int v);
   int xwarps;       // warps launched by the X pass (rows of `partials`)
-  int nvariants;    // variants of the strided passes (1, 2 or 4)
-  int widths[4];    // their column tile widths
-  int staged[4];    // 1: input tiles staged through shared memory by TMA
+  int nvariants;    // variants of the strided passes (at most 5)
+  int widths[5];    // their column tile widths
+  int staged[5];    // 1: input tiles staged through shared memory by TMA
+  unsigned vmask[SP_N];  // variants built for each pass (bit v)
 };
 
 const PassTable* table_f32(int N);

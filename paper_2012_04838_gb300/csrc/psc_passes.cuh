@@ -757,7 +757,11 @@ template <typename T, int N> struct Passes {
 #define PSC_STAGED 1
 #endif
   static constexpr bool STAGED = PSC_STAGED && sizeof(T) == 4 && N >= 64 && M % 2 == 0;
-  static constexpr int NV = STAGED ? 4 : (WV0 != WV1 ? 2 : 1);
+  // variant 4: staged, 16 columns, for the inverse passes where it fits one CTA
+  static constexpr bool STAGED16 = STAGED && StagedTile<T, N, 16, true>::SMEM <= 227 * 1024;
+  static constexpr int NV = STAGED16 ? 5 : STAGED ? 4 : (WV0 != WV1 ? 2 : 1);
+  static constexpr unsigned MASK_INV = (1u << NV) - 1u;
+  static constexpr unsigned MASK_FWD = STAGED16 ? 0xFu : (1u << NV) - 1u;
   template <int W, int PASS, bool STATS> static bool launch_s(const PassArgs& a) {
     if constexpr (STAGED) {
       using TL = StagedTile<T, N, W, PASS == SP_ZINV || PASS == SP_YINV>;
@@ -789,6 +793,9 @@ template <typename T, int N> struct Passes {
   template <int PASS> static bool staged(const PassArgs& a, bool stats, int v) {
     if constexpr (PASS == SP_ZINV || PASS == SP_YINV) {
       if (v == 2) return stats ? launch_s<4, PASS, true>(a) : launch_s<4, PASS, false>(a);
+      if constexpr (STAGED16) {
+        if (v == 4) return stats ? launch_s<16, PASS, true>(a) : launch_s<16, PASS, false>(a);
+      }
       return stats ? launch_s<8, PASS, true>(a) : launch_s<8, PASS, false>(a);
     } else {
       (void)stats;
@@ -864,7 +871,8 @@ template <typename T, int N> struct Passes {
   static const PassTable* table() {
     static const PassTable tb = {&zinv, &yinv, &xpass, &yfwd, &zfwd,
                                  xgrid() * (X2 ? 4 : XCfg<T, N>::WARPS), NV,
-                                 {WV0, WV1, 4, 8}, {0, 0, 1, 1}};
+                                 {WV0, WV1, 4, 8, 16}, {0, 0, 1, 1, 1},
+                                 {MASK_INV, MASK_INV, MASK_FWD, MASK_FWD}};
     return &tb;
   }
 };

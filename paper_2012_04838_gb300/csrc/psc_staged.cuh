@@ -48,7 +48,9 @@ template <typename T, int N, int W, bool INV> struct StagedTile {
   static constexpr size_t SMEM = BAR_OFF + sizeof(unsigned long long);
   // CTAs per SM that fit its 228 KB of shared memory (1 KB reserved per CTA)
   static constexpr int FIT = (int)((228 * 1024) / (SMEM + 1024));
-  static constexpr int MINB = FIT < 1 ? 1 : (FIT > 4 ? 4 : FIT);
+  // no more CTAs than leave every thread 128 registers
+  static constexpr int RFIT = 512 / (W * PlanD<N>::TPL) < 1 ? 1 : 512 / (W * PlanD<N>::TPL);
+  static constexpr int MINB = FIT < 1 ? 1 : (FIT < RFIT ? FIT : RFIT);
   static_assert(BOX_BYTES % 128 == 0, "boxes start 128-byte aligned");
   static_assert(W * sizeof(C) % 16 == 0, "a box row is a multiple of 16 bytes");
 };

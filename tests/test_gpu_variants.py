@@ -25,15 +25,20 @@ def dev():
     return torch.device("cuda:0")
 
 
-def n_variants(N, prec):
+def variant_codes(N, prec):
+    """PSC_STRIDED_VARIANT codes (z-inverse, y-inverse, y-forward, z-forward)
+    covering every variant built for the grid: 0/1 unstaged 8/16 columns,
+    2/3 staged 4/8 columns, 4 staged 16 columns (inverse passes only)."""
     if prec == B.FP64:
-        return 1
+        return ["0000"]
     M = (N - 1) // 3 + 1
-    return 4 if N >= 64 and M % 2 == 0 else 2
+    if N >= 64 and M % 2 == 0:
+        return ["0000", "1111", "2222", "3333", "4433"]
+    return ["0000", "1111"]
 
 
 def run_variant(dev, monkeypatch, p, x, v):
-    monkeypatch.setenv("PSC_STRIDED_VARIANT", str(v))
+    monkeypatch.setenv("PSC_STRIDED_VARIANT", v)
     sim = B.Simulation(p, device=dev)
     try:
         staged = sim.tile_staged()
@@ -49,8 +54,9 @@ def run_variant(dev, monkeypatch, p, x, v):
 def test_variants_agree_bit_for_bit(dev, monkeypatch, N):
     p = B.Params(N=N, precision=B.FP32_MIXED, nu=0.013, Sc=0.7, beta=1.1, eps_inj=0.1, kF=2.0, dt=1e-3)
     x = random_compact_state(N, 300 + N, kpeak=6.0).astype(np.complex64)
-    nv = n_variants(N, B.FP32_MIXED)
-    out = [run_variant(dev, monkeypatch, p, x, v) for v in range(nv)]
+    codes = variant_codes(N, B.FP32_MIXED)
+    nv = len(codes)
+    out = [run_variant(dev, monkeypatch, p, x, c) for c in codes]
     for v in range(nv):
         assert all(out[v][0].values()) == (v >= 2), (v, out[v][0])
     for v in range(1, nv):
@@ -59,9 +65,10 @@ def test_variants_agree_bit_for_bit(dev, monkeypatch, N):
         np.testing.assert_array_equal(out[v][4], out[0][4])
         for k in ("K", "eps", "eps_phys", "chi", "chi_phys", "skew", "flat", "phi_var"):
             assert out[v][2][k] == out[0][2][k], (v, k)
-    monkeypatch.setenv("PSC_STRIDED_VARIANT", str(nv))
-    with pytest.raises(B.PscError):
-        B.Simulation(p, device=dev)
+    for bad in ("5", "4444", "12"):  # not built / not for the forward passes / malformed
+        monkeypatch.setenv("PSC_STRIDED_VARIANT", bad)
+        with pytest.raises(B.PscError):
+            B.Simulation(p, device=dev)
 
 
 def test_variants_agree_bit_for_bit_1024(dev, monkeypatch):
@@ -74,8 +81,8 @@ def test_variants_agree_bit_for_bit_1024(dev, monkeypatch):
     x = torch.view_as_complex(torch.randn((4, P, P, M, 2), generator=g, device=dev, dtype=torch.float32)) * 1e3
     x[:, :, :, 0] = 0  # keep the kx = 0 plane trivially Hermitian
     ref = None
-    for v in range(4):
-        monkeypatch.setenv("PSC_STRIDED_VARIANT", str(v))
+    for v in variant_codes(N, B.FP32_MIXED):
+        monkeypatch.setenv("PSC_STRIDED_VARIANT", v)
         sim = B.Simulation(p, device=dev)
         try:
             r = sim.rhs(x)
