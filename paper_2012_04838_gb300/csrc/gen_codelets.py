@@ -12,8 +12,26 @@ import sys
 
 SIZES = (2, 3, 4, 6, 8, 12, 16, 24, 32)
 
+# Two-step plans N = R1 * R2 of the strided passes (must match Plan<N> in
+# psc_common.cuh).  An inverse pass zero-pads its lines from 2K+1 to N points
+# (K = (N-1)//3), so inputs n1 of its first DFT (positions R2 n1 + n2) are zero
+# for every n2 when R2 n1 > K and R2 n1 + R2 - 1 < N - K: those DFTs are also
+# generated with that input range known to be zero.
+PLANS = {8: (4, 2), 12: (4, 3), 16: (4, 4), 24: (6, 4), 32: (8, 4), 48: (12, 4), 64: (8, 8),
+         96: (12, 8), 128: (16, 8), 192: (24, 8), 256: (16, 16), 512: (32, 16), 1024: (32, 32)}
+
+
+def zero_range(N):
+    R1, R2 = PLANS[N]
+    K = (N - 1) // 3
+    zs = [n1 for n1 in range(R1) if R2 * n1 > K and R2 * n1 + R2 - 1 < N - K]
+    return (R1, zs[0], zs[-1]) if zs else None
+
 
 class Emitter:
+    """Emits straight-line code; a value None is a known zero, which the
+    operations propagate instead of computing."""
+
     def __init__(self):
         self.lines = []
         self.n = 0
@@ -25,13 +43,23 @@ class Emitter:
         return (v + "r", v + "i")
 
     def add(self, a, b):
+        if a is None:
+            return b
+        if b is None:
+            return a
         return self.new(f"{a[0]} + {b[0]}", f"{a[1]} + {b[1]}")
 
     def sub(self, a, b):
+        if b is None:
+            return a
+        if a is None:
+            return self.new(f"-{b[0]}", f"-{b[1]}")
         return self.new(f"{a[0]} - {b[0]}", f"{a[1]} - {b[1]}")
 
     def rot(self, a, q):
         """a * i^q without arithmetic (negations fold into later adds)."""
+        if a is None:
+            return None
         q %= 4
         if q == 0:
             return a
@@ -43,6 +71,8 @@ class Emitter:
 
     def twiddle(self, a, m, R, s):
         """a * exp(s*2*pi*i*m/R)."""
+        if a is None:
+            return None
         m %= R
         if m == 0:
             return a
@@ -68,10 +98,15 @@ class Emitter:
         if R == 3:
             a, b, c = xs
             t1 = self.add(b, c)
-            t2 = self.new(f"{a[0]} - T(0.5) * {t1[0]}", f"{a[1]} - T(0.5) * {t1[1]}")
+            if t1 is None:
+                t2 = a
+            elif a is None:
+                t2 = self.new(f"-T(0.5) * {t1[0]}", f"-T(0.5) * {t1[1]}")
+            else:
+                t2 = self.new(f"{a[0]} - T(0.5) * {t1[0]}", f"{a[1]} - T(0.5) * {t1[1]}")
             h = 0.86602540378443865 * s  # s * sqrt(3)/2
             d = self.sub(b, c)
-            t3 = self.new(f"-T({h!r}) * {d[1]}", f"T({h!r}) * {d[0]}")
+            t3 = None if d is None else self.new(f"-T({h!r}) * {d[1]}", f"T({h!r}) * {d[0]}")
             return [self.add(a, t1), self.add(t2, t3), self.sub(t2, t3)]
         if R == 4:
             a, b, c, d = xs
@@ -94,30 +129,51 @@ class Emitter:
         return X
 
 
-def codelet(R, s):
+def codelet(R, s, zero=None):
+    """zero = (z0, z1): inputs z0..z1 are known to be zero and are not read."""
     e = Emitter()
     xs = []
     for i in range(R):
+        if zero and zero[0] <= i <= zero[1]:
+            xs.append(None)
+            continue
         e.lines.append(f"    const T in{i}r = x[{i}].x, in{i}i = x[{i}].y;")
         xs.append((f"in{i}r", f"in{i}i"))
     X = e.dft(xs, s)
     for k in range(R):
-        e.lines.append(f"    x[{k}].x = {X[k][0]}; x[{k}].y = {X[k][1]};")
+        if X[k] is None:
+            e.lines.append(f"    x[{k}].x = T(0); x[{k}].y = T(0);")
+        else:
+            e.lines.append(f"    x[{k}].x = {X[k][0]}; x[{k}].y = {X[k][1]};")
     name = "fwd" if s < 0 else "inv"
     body = "\n".join(e.lines)
-    return (f"template <> struct Dft<{R}, {s}> {{\n"
-            f"  template <typename T, typename C>\n"
-            f"  static __device__ __forceinline__ void run(C* x) {{  // {name} {R}\n{body}\n  }}\n}};\n")
+    if zero:
+        head = f"template <> struct DftZ<{R}, {s}, {zero[0]}, {zero[1]}> {{\n"
+        name += f" {R}, inputs {zero[0]}..{zero[1]} zero"
+    else:
+        head = f"template <> struct Dft<{R}, {s}> {{\n"
+        name += f" {R}"
+    return (head + f"  template <typename T, typename C>\n"
+            f"  static __device__ __forceinline__ void run(C* x) {{  // {name}\n{body}\n  }}\n}};\n")
 
 
 def main(out=sys.stdout):
     out.write("// Generated by gen_codelets.py -- do not edit.\n")
     out.write("// In-place, in-register DFTs: X[k] = sum_n x[n] exp(s 2 pi i n k / R).\n")
     out.write("#pragma once\n\nnamespace psc {\n\n")
-    out.write("template <int R, int S> struct Dft;\n\n")
+    out.write("template <int R, int S> struct Dft;\n")
+    out.write("// inputs Z0..Z1 known to be zero\n")
+    out.write("template <int R, int S, int Z0, int Z1> struct DftZ;\n\n")
     for R in SIZES:
         for s in (-1, 1):
             out.write(codelet(R, s))
+            out.write("\n")
+    done = set()
+    for N in sorted(PLANS):
+        z = zero_range(N)
+        if z and z not in done:
+            done.add(z)
+            out.write(codelet(z[0], 1, (z[1], z[2])))
             out.write("\n")
     out.write("}  // namespace psc\n")
 

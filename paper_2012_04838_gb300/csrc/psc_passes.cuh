@@ -69,8 +69,43 @@ __device__ __forceinline__ typename CT<T>::type* strided_twiddles(unsigned char*
   return t;
 }
 
+// Inputs n1 of the first DFT of an inverse (zero-padded) line that are zero
+// for every n2: positions R2 n1 + n2 all lie in the band K < p < N - K.  The
+// codelet generator emits DftZ<R1, +1, Z0, Z1> for exactly this range.
+template <int N> struct ZeroInputs {
+  static constexpr int R1 = PlanD<N>::R1, R2 = PlanD<N>::R2, K = (N - 1) / 3;
+  __host__ __device__ static constexpr bool zero(int n1) { return R2 * n1 > K && R2 * n1 + R2 - 1 < N - K; }
+  __host__ __device__ static constexpr int first() {
+    for (int n1 = 0; n1 < R1; ++n1)
+      if (zero(n1)) return n1;
+    return R1;
+  }
+  __host__ __device__ static constexpr int last() {
+    for (int n1 = R1 - 1; n1 >= 0; --n1)
+      if (zero(n1)) return n1;
+    return -1;
+  }
+  static constexpr int Z0 = first(), Z1 = last();
+  static constexpr bool ANY = Z0 <= Z1;
+};
+
+// First DFT of a line: the pruned codelet for an inverse pass, else the full one.
+template <typename T, int N, int DIR, class C> __device__ __forceinline__ void first_dft(C (&a)[PlanD<N>::R1]) {
+  if constexpr (DIR > 0 && ZeroInputs<N>::ANY)
+    DftZ<PlanD<N>::R1, DIR, ZeroInputs<N>::Z0, ZeroInputs<N>::Z1>::template run<T, C>(a);
+  else
+    Dft<PlanD<N>::R1, DIR>::template run<T, C>(a);
+}
+
+// True if no output k1 + R1 k2 (k1 < R1) of a length-N line is a retained
+// wavenumber (K < k < N - K): a forward pass need not compute it.
+template <int N> __host__ __device__ constexpr bool dead_k2(int k2) {
+  return PlanD<N>::R1 * k2 > (N - 1) / 3 && PlanD<N>::R1 * k2 + PlanD<N>::R1 - 1 < N - (N - 1) / 3;
+}
+
 // One length-N DFT per column, direction DIR (-1 forward, +1 inverse).
 // ld(p) returns the element at line position p; st(k, v) stores output k.
+// A forward transform only computes the outputs a truncated pass can keep.
 template <typename T, int N, int W, int DIR, class LD, class ST>
 __device__ __forceinline__ void strided_fft(const LD& ld, const ST& st,
                                             typename CT<T>::type* sm,
@@ -84,9 +119,12 @@ __device__ __forceinline__ void strided_fft(const LD& ld, const ST& st,
   for (int j = 0; j < J1; ++j) {
     const int n2 = t + j * TPL;
     C a[R1];
-#pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) a[n1] = ld(R2 * n1 + n2);
-    Dft<R1, DIR>::template run<T, C>(a);
+    static_for<0, R1>([&](auto nc) {
+      constexpr int n1 = decltype(nc)::value;
+      if constexpr (DIR > 0 && ZeroInputs<N>::zero(n1)) a[n1] = mk(T(0), T(0));  // not read
+      else a[n1] = ld(R2 * n1 + n2);
+    });
+    first_dft<T, N, DIR>(a);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       C v = a[k1];
@@ -105,8 +143,10 @@ __device__ __forceinline__ void strided_fft(const LD& ld, const ST& st,
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2) b[n2] = sm[k1 * SM::ROW + n2 * W + w];
     Dft<R2, DIR>::template run<T, C>(b);
-#pragma unroll
-    for (int k2 = 0; k2 < R2; ++k2) st(k1 + R1 * k2, b[k2]);
+    static_for<0, R2>([&](auto kc) {
+      constexpr int k2 = decltype(kc)::value;
+      if constexpr (!(DIR < 0 && dead_k2<N>(k2))) st(k1 + R1 * k2, b[k2]);
+    });
   }
   __syncthreads();
 }

@@ -69,7 +69,7 @@ __device__ __forceinline__ void strided_fft_regs(typename CT<T>::type (&in)[Plan
 #pragma unroll
   for (int j = 0; j < J1; ++j) {
     const int n2 = t + j * TPL;
-    Dft<R1, DIR>::template run<T, C>(in[j]);
+    first_dft<T, N, DIR>(in[j]);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       C v = in[j][k1];
@@ -88,8 +88,10 @@ __device__ __forceinline__ void strided_fft_regs(typename CT<T>::type (&in)[Plan
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2) b[n2] = sm[k1 * SM::ROW + n2 * W + w];
     Dft<R2, DIR>::template run<T, C>(b);
-#pragma unroll
-    for (int k2 = 0; k2 < R2; ++k2) st(k1 + R1 * k2, b[k2]);
+    static_for<0, R2>([&](auto kc) {
+      constexpr int k2 = decltype(kc)::value;
+      if constexpr (!(DIR < 0 && dead_k2<N>(k2))) st(k1 + R1 * k2, b[k2]);
+    });
   }
   __syncthreads();
 }
@@ -203,10 +205,12 @@ k_strided_s(PassArgs a, const __grid_constant__ CUtensorMap tm) {
     C in[J1][R1];
 #pragma unroll
     for (int j = 0; j < J1; ++j)
-#pragma unroll
-      for (int n1 = 0; n1 < R1; ++n1) {
+      static_for<0, R1>([&](auto nc) {
+        constexpr int n1 = decltype(nc)::value;
         const int p = R2 * n1 + t + j * TPL;
-        if constexpr (INV) {
+        if constexpr (INV && ZeroInputs<N>::zero(n1)) {
+          in[j][n1] = zero;  // in the zero band for every column: not read
+        } else if constexpr (INV) {
           int k;
           if (!act || !k_of_pos<N>(p, k)) {
             in[j][n1] = zero;
@@ -228,7 +232,7 @@ k_strided_s(PassArgs a, const __grid_constant__ CUtensorMap tm) {
         } else {
           in[j][n1] = stg[p * W + w];
         }
-      }
+      });
     __syncthreads();  // the staging tile is free
     if (leader && tr + 1 < SPL::NT) issue(tr + 1);
     if constexpr (PASS == SP_ZINV) {
