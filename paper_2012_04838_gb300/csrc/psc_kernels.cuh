@@ -218,9 +218,11 @@ __device__ __forceinline__ long long isqrt_floor(long long a) {
 }
 
 // Shell n = floor(|k| + 1/2), i.e. n^2 - n < |k|^2 <= n^2 + n.  One CTA per
-// shell sums, in a fixed order, w |u|^2, w |phi|^2, |k|^2 w |u|^2,
-// |k|^2 w |phi|^2 and w Re(conj(phi) u2) over the shell's stored modes
-// (w = 1 at kx = 0, else 2).  out[q * nshell + n] holds the raw sums.
+// shell sums w |u|^2, w |phi|^2, |k|^2 w |u|^2, |k|^2 w |phi|^2 and
+// w Re(conj(phi) u2) over the shell's stored modes (w = 1 at kx = 0, else 2).
+// Each thread accumulates in the state's precision (compensated sums in FP32,
+// since FP64 arithmetic is slow on this part), then the CTA adds the threads'
+// sums in FP64 in a fixed order.  out[q * nshell + n] holds the raw sums.
 template <typename T>
 __global__ void __launch_bounds__(256) k_shells(Dims d, const void* u_, const void* phi_, int nshell,
                                                double* out) {
@@ -233,7 +235,11 @@ __global__ void __launch_bounds__(256) k_shells(Dims d, const void* u_, const vo
   const long long hi = n == 0 ? 0 : (long long)n * n + n;   // inclusive
   const int kb = (n + 1) < d.K ? (n + 1) : d.K;
   const int side = 2 * kb + 1;
-  double acc[NSQ] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  MomentSum<T> acc[NSQ];
+  // amplitudes are summed as u_hat / N^3 (order-one numbers, far from the FP32
+  // range limits); the raw sums are restored in FP64 at the end
+  const double n3 = (double)d.N * d.N * d.N;
+  const T sc = (T)(1.0 / n3);
   for (int q = threadIdx.x; q < side * side; q += blockDim.x) {
     const int kz = q / side - kb, ky = q % side - kb;
     const long long r2 = (long long)kz * kz + (long long)ky * ky;
@@ -244,25 +250,24 @@ __global__ void __launch_bounds__(256) k_shells(Dims d, const void* u_, const vo
     const long long base = ((long long)(kz + d.K) * d.P + (ky + d.K)) * d.M;
     for (long long kx = x0; kx <= x1; ++kx) {
       const long long i = base + kx;
-      const double w = kx == 0 ? 1.0 : 2.0;
-      const double k2 = (double)(r2 + kx * kx);
-      const C a = u[i], b = u[d.S + i], c = u[2 * d.S + i];
-      const double eu = w * ((double)a.x * a.x + (double)a.y * a.y + (double)b.x * b.x +
-                             (double)b.y * b.y + (double)c.x * c.x + (double)c.y * c.y);
-      acc[0] += eu;
-      acc[2] += k2 * eu;
+      const T w = kx == 0 ? T(1) : T(2);
+      const T k2 = (T)(r2 + kx * kx);  // exact: |k|^2 < 2^24
+      const C a = cscale(u[i], sc), b = cscale(u[d.S + i], sc), c = cscale(u[2 * d.S + i], sc);
+      const T eu = w * (a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y + c.x * c.x + c.y * c.y);
+      acc[0].add(eu);
+      acc[2].add(k2 * eu);
       if (phi) {
-        const C p = phi[i];
-        const double ep = w * ((double)p.x * p.x + (double)p.y * p.y);
-        acc[1] += ep;
-        acc[3] += k2 * ep;
-        acc[4] += w * ((double)p.x * b.x + (double)p.y * b.y);
+        const C p = cscale(phi[i], sc);
+        const T ep = w * (p.x * p.x + p.y * p.y);
+        acc[1].add(ep);
+        acc[3].add(k2 * ep);
+        acc[4].add(w * (p.x * b.x + p.y * b.y));
       }
     }
   }
   for (int q = 0; q < NSQ; ++q) {
-    const double s = block_sum(acc[q], sm);
-    if (threadIdx.x == 0) out[q * nshell + n] = s;
+    const double s = block_sum(acc[q].value(), sm);
+    if (threadIdx.x == 0) out[q * nshell + n] = s * n3 * n3;
     __syncthreads();
   }
 }
