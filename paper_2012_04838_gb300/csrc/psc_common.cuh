@@ -165,11 +165,29 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, unsigned pa
       : "memory");
   return ok != 0;
 }
-// wait for the phase of parity `parity` to complete; false after ~2^22 polls
-__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity) {
-  for (int i = 0; i < (1 << 22); ++i)
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// wait for the phase of parity `parity` to complete; false once about two
+// seconds have passed (a time bound, whatever each poll's own suspend time),
+// or as soon as bit 2 of *abort is seen set (another wait already gave up)
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity,
+                                          const int* abort = nullptr) {
+  if (mbar_try_wait(b, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned i = 1;; ++i) {
     if (mbar_try_wait(b, parity)) return true;
-  return false;
+    if ((i & 255u) == 0) {
+      if (abort && (*(const volatile int*)abort & 4)) return false;
+      if (global_ns() - t0 > 2000000000ull) return false;
+    }
+  }
+}
+// one arrival on an mbarrier (release: this thread's earlier accesses first)
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
 }
 // AND of `pred` over the `count` threads of named barrier `id` (a barrier too)
 __device__ __forceinline__ bool bar_and(int id, int count, bool pred) {

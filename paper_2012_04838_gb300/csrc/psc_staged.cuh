@@ -57,7 +57,9 @@ template <typename T, int N, int W, bool INV> struct StagedTile {
 
 // One length-N DFT per column from step-1 inputs already in registers:
 // in[j][n1] is line position R2 n1 + t + j TPL.  Same steps as strided_fft,
-// with the step-1 twiddles wN^(n2 k1) read from the global table tw.
+// with the step-1 twiddles wN^(n2 k1) read from the global table tw.  It does
+// not end with a barrier: the caller's next CTA barrier must come before the
+// exchange buffer is written again.
 template <typename T, int N, int W, int DIR, class ST>
 __device__ __forceinline__ void strided_fft_regs(typename CT<T>::type (&in)[PlanD<N>::J1][PlanD<N>::R1],
                                                  const ST& st, typename CT<T>::type* sm,
@@ -93,7 +95,6 @@ __device__ __forceinline__ void strided_fft_regs(typename CT<T>::type (&in)[Plan
       if constexpr (!(DIR < 0 && dead_k2<N>(k2))) st(k1 + R1 * k2, b[k2]);
     });
   }
-  __syncthreads();
 }
 
 // Transform tr of a pass: source field / stream, how its line is formed, and
@@ -194,11 +195,17 @@ k_strided_s(PassArgs a, const __grid_constant__ CUtensorMap tm) {
   for (int tr = 0; tr < SPL::NT; ++tr) {
     int src, kind, s2, out;
     SPL::get(tr, src, kind, s2, out);
-    if (!__syncthreads_and(mbar_wait(bar, parity))) {
+    // one thread polls the barrier while the others wait at the CTA barrier
+    // (which also orders the last transform's exchange reads before this
+    // one's writes); the barrier makes the tile visible to every thread
+    const bool landed = mbar_wait(bar, parity, &a.ctrl->err);
+    if (!__syncthreads_and(landed)) {
       // the tile did not arrive in time: report, give it a bounded time to
       // land in this CTA's shared memory, and stop
-      if (leader) atomicOr(&a.ctrl->err, 4);
-      mbar_wait(bar, parity);
+      if (leader) {
+        atomicOr(&a.ctrl->err, 4);
+        mbar_wait(bar, parity);
+      }
       return;
     }
     parity ^= 1u;

@@ -543,7 +543,9 @@ __global__ void __launch_bounds__(X2SCfg<T, N>::THREADS, 1) k_xpass2s(PassArgs a
 #pragma unroll 1
   for (; line < nlines; line += stride) {
     const long long next = line + stride;
-    ok = bar_and(q.bar, TH, mbar_wait(barA, pa));
+    // the row's first thread polls; the row barrier shares the outcome and
+    // makes the staged streams visible to the row's threads
+    ok = bar_and(q.bar, TH, leader ? mbar_wait(barA, pa, &a.ctrl->err) : true);
     if (!ok) break;
     pa ^= 1u;
     ia = false;
@@ -557,7 +559,7 @@ __global__ void __launch_bounds__(X2SCfg<T, N>::THREADS, 1) k_xpass2s(PassArgs a
           }
         },
         [&] {
-          const bool w = bar_and(q.bar, TH, mbar_wait(barB, pb));
+          const bool w = bar_and(q.bar, TH, leader ? mbar_wait(barB, pb, &a.ctrl->err) : true);
           if (w) {
             pb ^= 1u;
             ib = false;
@@ -576,9 +578,11 @@ __global__ void __launch_bounds__(X2SCfg<T, N>::THREADS, 1) k_xpass2s(PassArgs a
   if (!ok) {
     // a copy did not complete in time: report it, give copies still in flight
     // a bounded time to land in this CTA's shared memory, and stop
-    if (leader) atomicOr(&a.ctrl->err, 4);
-    if (ia) mbar_wait(barA, pa);
-    if (ib) mbar_wait(barB, pb);
+    if (leader) {
+      atomicOr(&a.ctrl->err, 4);
+      if (ia) mbar_wait(barA, pa);
+      if (ib) mbar_wait(barB, pb);
+    }
   }
   if (a.want_umax) {
     double umax = (double)um * (double)scale;
