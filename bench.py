@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-cufft", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--companion", action="store_true",
+                    help="512^3 FP32-mixed and FP64 from the same IC, 200 steps, records compared "
+                         "every 10 steps (error check of the 1024^3 FP32-mixed run)")
     ap.add_argument("--long-run", action="store_true",
                     help="only run 256^3 FP32-mixed and FP64 side by side for 2000 steps and "
                          "print their statistical agreement")
@@ -360,12 +363,61 @@ def run_long(N=256, steps=2000, every=10):
     return out
 
 
+def run_companion(N=512, steps=200, every=10):
+    """FP32-mixed against FP64 at 512^3 from the same IC (the 1024^3 workload's
+    spectrum, forcing, Sc and CFL 0.5, nu for k_max eta = 1.5): the largest relative
+    difference over the records of K, epsilon, chi, and of E(k) for
+    k <= k_max/2, plus the state difference at the end."""
+    import numpy as np
+    import torch
+    import paper_2012_04838_gb300 as psc
+    from paper_2012_04838_gb300.serve import nu_for_resolution
+    res = {}
+    out = {"N": N, "steps": steps, "record_every": every, "nu": nu_for_resolution(N, 1.5)}
+    for name, prec in (("fp32_mixed", psc.FP32_MIXED), ("fp64", psc.FP64)):
+        p = psc.Params(N=N, precision=prec, nu=out["nu"], Sc=1.0, beta=1.0, kF=2.0, eps_inj=0.1,
+                       cfl=0.5, ic=psc.IC_SPECTRUM_K4, seed=3, ic_energy=1.5, record_every=every)
+        sim = psc.Simulation(p, device="cuda:0")
+        sim.init_field()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        recs, spec = [], []
+        for n in range(0, steps + 1, every):
+            if n:
+                sim.step(every)
+            r, E, _ = sim.stats()
+            recs.append(r)
+            spec.append(E)
+        out[name + "_wall_s"] = time.perf_counter() - t0
+        state = sim.get_state().cpu().numpy().astype(np.complex128)
+        res[name] = (recs, np.array(spec), state)
+        sim.close()
+        torch.cuda.empty_cache()
+    (r32, E32, s32), (r64, E64, s64) = res["fp32_mixed"], res["fp64"]
+    kh = int((N / 3) / 2)
+    for q in ("K", "eps", "chi"):
+        out[q + "_max_rel_diff"] = float(max(abs(a[q] - b[q]) / abs(b[q]) for a, b in zip(r32, r64) if b[q] != 0))
+    # shells whose energy is still at round-off level (the IC spectrum decays
+    # like exp(-2 (k/4)^2)) are left out: E >= 1e-8 of the record's peak
+    a, b = E32[:, 1:kh + 1], E64[:, 1:kh + 1]
+    live = b >= 1e-8 * b.max(axis=1, keepdims=True)
+    out["E_max_rel_diff_k_le_kmax_over_2"] = float(np.max(np.abs(a - b)[live] / b[live]))
+    out["E_shells_compared_first_last"] = [int(live[0].sum()), int(live[-1].sum())]
+    out["final_state_rel_l2_diff"] = float(np.linalg.norm(s32 - s64) / np.linalg.norm(s64))
+    out["t_end"] = r64[-1]["t"]
+    out["dt_fp32_fp64"] = [r32[-1]["dt"], r64[-1]["dt"]]
+    return out
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
     if a.long_run:
         print(json.dumps({"long_run": run_long()}), flush=True)
+        return 0
+    if a.companion:
+        print(json.dumps({"companion_512": run_companion()}), flush=True)
         return 0
 
     import torch

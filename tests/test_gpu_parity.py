@@ -159,6 +159,44 @@ def test_20_step_trajectory_matches_oracle(dev, N, integ, prec):
 
 
 @pytest.mark.parametrize("prec", PREC, ids=PNAME.get)
+def test_config_c1_full_run_matches_oracle(dev, prec):
+    """The small configuration end to end: 32^3 Taylor-Green plus 1% k^4 noise,
+    nu = 0.02, Sc = 1, beta = 1, constant power 0.1 on |k|^2 <= 4, dt = 0.005,
+    200 steps, a record every 10 steps (21 records with spectra)."""
+    N = 32
+    p = B.Params(N=N, precision=prec, nu=0.02, Sc=1.0, beta=1.0, eps_inj=0.1, kF=2.0, dt=0.005,
+                 ic=B.IC_TAYLOR_GREEN_NOISE, seed=1, record_every=10)
+    sim = B.Simulation(p, device=dev)
+    sim.init_field()
+    got = []
+    for n in range(0, 201, 10):
+        if n:
+            sim.step(10)
+        got.append(sim.stats())
+    uh, ph, recs, t, _ = O.run(oparams(p), 200, with_records=True)
+    assert len(recs) == len(got) == 21
+    tol = 1e-10 if prec == B.FP64 else 2e-4
+    keys = ("K", "eps", "eps_phys", "chi", "chi_phys", "phi_var", "phi_prod", "A", "E_forced")
+    # scalar quantities start from exactly zero (phi = 0 at t = 0): an absolute
+    # floor relative to each quantity's largest value over the run
+    scale = {k: max(abs(r[k]) for r in recs) for k in keys}
+    for (rec, E, Ep), ref in zip(got, recs):
+        assert rec["step"] == ref["step"]
+        assert abs(rec["t"] - ref["t"]) <= 1e-12 * max(1.0, ref["t"])
+        for k in keys:
+            assert abs(rec[k] - ref[k]) <= tol * abs(ref[k]) + 1e-12 * scale[k], (ref["step"], k, rec[k], ref[k])
+        assert np.allclose(E, ref["E"], rtol=tol, atol=tol * ref["E"].max())
+        if ref["Ephi"].max() > 0:
+            assert np.allclose(Ep, ref["Ephi"], rtol=tol, atol=tol * ref["Ephi"].max())
+        sk = 1e-8 if prec == B.FP64 else 2e-3
+        assert np.allclose(rec["skew"], ref["skew"], rtol=sk, atol=sk), (ref["step"], rec["skew"], ref["skew"])
+        assert np.allclose(rec["flat"], ref["flat"], rtol=sk, atol=sk), (ref["step"], rec["flat"], ref["flat"])
+    ref = full_to_compact(np.concatenate([uh, ph[None]]), N)
+    final = sim.get_state().cpu().numpy().astype(np.complex128)
+    assert rel(final, ref) < (1e-10 if prec == B.FP64 else 1e-3)
+
+
+@pytest.mark.parametrize("prec", PREC, ids=PNAME.get)
 def test_cfl_controlled_run_matches_oracle(dev, prec):
     N = 32
     p = B.Params(N=N, precision=prec, nu=0.01, cfl=0.5, record_every=5, ic=B.IC_SPECTRUM_K4,
