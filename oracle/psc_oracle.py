@@ -19,7 +19,9 @@ Readings of the paper that the oracle adopts (the GPU path adopts the same):
   * rotational nonlinear term ``P(u x omega)`` (equal to ``-P(u.grad u)`` on
     the retained set; both forms are implemented and their agreement is a test).
   * constant-power forcing ``A = eps_inj / (2 E_f)`` on the sphere
-    ``0 < |k|^2 <= k_F^2``, evaluated at every stage input.
+    ``0 < |k|^2 <= k_F^2``, evaluated at every stage input; or the paper's
+    deterministic variant (section 2.3), applied after the last stage: the
+    band is rescaled so that its energy stays at its value at the first step.
   * Lawson integrating-factor RK4 for the viscous/diffusive terms; plain
     explicit RK4 (section 2.2) as the alternative integrator.
   * shells ``n = floor(|k| + 1/2)``; ``E(n) = sum w_k |u_k|^2 / (2 N^6)``.
@@ -40,6 +42,7 @@ import numpy as np
 
 FORCE_NONE = 0
 FORCE_CONST_POWER = 1
+FORCE_HOLD_ENERGY = 2       # the paper's deterministic scheme: band energy held after each step
 
 IC_SPECTRUM_K4 = 0          # E(k) ~ k^4 exp(-2 (k/4)^2), random phases
 IC_TAYLOR_GREEN_NOISE = 1   # Taylor-Green vortex plus the k^4 noise
@@ -211,6 +214,19 @@ def forced_energy(uh, g: Grid, kF: float) -> float:
     return float(np.sum(np.where(b, g.w * e, 0.0)) / (2.0 * g.N ** 6))
 
 
+def hold_band_energy(uh, g: Grid, kF: float, Ef0: float):
+    """The deterministic forcing of section 2.3, applied after the last RK
+    stage: the modes of the sphere 0 < |k| <= kF are multiplied by
+    f = sqrt(Ef0 / E_f) so that the band energy returns to Ef0 (E_f the band
+    energy after the step; f = 1 if the band is empty).  Multiplying by f over
+    a step of length dt is forcing with the rate A = ln(f) / dt, which injects
+    2 A E_f.  Returns the rescaled velocity and f."""
+    ef = forced_energy(uh, g, kF)
+    f = math.sqrt(Ef0 / ef) if ef > 1e-300 else 1.0
+    b = band(g, kF)
+    return np.array([np.where(b, f * uh[c], uh[c]) for c in range(3)]), f
+
+
 def forcing_amplitude(uh, g: Grid, p: Params) -> float:
     """A of Eq. 1 for constant-power forcing: A u_hat on the band injects
     2 A E_f = eps_inj per unit time.  A = 0 when the band holds no energy."""
@@ -362,7 +378,8 @@ def _moments(a: np.ndarray):
     return m2, skew, flat
 
 
-def stats(uh, ph, g: Grid, p: Params, t: float = 0.0, dt: float | None = None) -> dict:
+def stats(uh, ph, g: Grid, p: Params, t: float = 0.0, dt: float | None = None,
+          A_hold: float = 0.0) -> dict:
     """One statistics record of the current state (section 2.3).
 
     Table 1: K = <u.u>/2, eps = 2 nu <S:S>, eta = (nu^3/eps)^(1/4),
@@ -370,7 +387,9 @@ def stats(uh, ph, g: Grid, p: Params, t: float = 0.0, dt: float | None = None) -
     l0 = u_rms^3/eps, T_e = l0/u_rms.  Eqs. 11-12: skewness and flatness of
     du_i/dx_i and of dphi/dx_i.  Eq. 13: <phi^2>, production -2 beta <phi u2>
     and chi = 2 D <grad phi . grad phi>.  eps and chi are formed both from the
-    spectrum and from grid averages; they agree for dealiased fields."""
+    spectrum and from grid averages; they agree for dealiased fields.
+    With the deterministic forcing, A is the rate of the last step's band
+    rescaling (A_hold, 0 before the first step)."""
     if dt is None:
         dt = p.dt
     N = g.N
@@ -411,7 +430,7 @@ def stats(uh, ph, g: Grid, p: Params, t: float = 0.0, dt: float | None = None) -
     lam = urms * math.sqrt(15.0 * p.nu / eps) if eps > 0 else float("inf")
     l0 = urms ** 3 / eps if eps > 0 else float("inf")
     umax = float(np.max(np.abs(u[0]) + np.abs(u[1]) + np.abs(u[2])))
-    A = forcing_amplitude(uh, g, p)
+    A = A_hold if p.forcing == FORCE_HOLD_ENERGY else forcing_amplitude(uh, g, p)
     Ef = forced_energy(uh, g, p.kF)
     return dict(
         t=t, dt=dt, K=Kspec, K_phys=0.5 * float(np.mean(u[0] ** 2 + u[1] ** 2 + u[2] ** 2)),
@@ -556,23 +575,31 @@ def run(p: Params, nsteps: int, uh=None, ph=None, with_records: bool = True):
 
     With ``cfl > 0`` the step is reset to put Eq. 10 at ``cfl`` at step 0 and
     at every record step, and held in between.  Records are taken of the state
-    at every step n with n % record_every == 0 and of the final state."""
+    at every step n with n % record_every == 0 and of the final state.  With
+    the deterministic forcing the band energy of the starting state is held
+    after every step."""
     g = Grid(p.N)
     if uh is None:
         uh, ph = init_field(g, p)
     dt = p.dt
     t = 0.0
     recs = []
+    hold = p.forcing == FORCE_HOLD_ENERGY
+    Ef0 = forced_energy(uh, g, p.kF) if hold else 0.0  # the band energy to hold
+    A_hold = 0.0
     for n in range(nsteps):
         if n % p.record_every == 0:
             if p.cfl > 0:
                 dt = cfl_dt(uh, g, p.cfl)
             if with_records:
-                recs.append(dict(step=n, **stats(uh, ph, g, p, t, dt)))
+                recs.append(dict(step=n, **stats(uh, ph, g, p, t, dt, A_hold)))
         uh, ph = step(uh, ph, g, p, dt)
+        if hold:
+            uh, f = hold_band_energy(uh, g, p.kF, Ef0)
+            A_hold = math.log(f) / dt
         t += dt
     if with_records:
-        recs.append(dict(step=nsteps, **stats(uh, ph, g, p, t, dt)))
+        recs.append(dict(step=nsteps, **stats(uh, ph, g, p, t, dt, A_hold)))
     return uh, ph, recs, t, dt
 
 

@@ -175,6 +175,50 @@ def test_single_mode_shear_decays_exactly(integ):
     assert np.abs(ph).max() == 0.0
 
 
+@pytest.mark.parametrize("integ", [O.INTEG_IFRK4, O.INTEG_RK4])
+def test_hold_forcing_keeps_a_decaying_band_mode_exactly(integ):
+    # u = (sin y, 0, 0) lies in the forced sphere (|k| = 1 <= kF = 2) and only
+    # decays viscously (its u x omega is removed by P), by exp(-nu dt) per step
+    # under IF-RK4 and by R(-nu dt) under RK4.  Holding the band energy
+    # multiplies it back by exactly the inverse, so the state never changes and
+    # the equivalent forcing rate is A = nu (IF-RK4) or -ln R(-nu dt)/dt (RK4):
+    # the injected power 2 A E_f then equals the dissipation 2 nu |k|^2 E_f.
+    N, nu, dt, n = 16, 0.05, 0.01, 12
+    p = O.Params(N=N, nu=nu, forcing=O.FORCE_HOLD_ENERGY, kF=2.0, beta=0.0, integrator=integ,
+                 dt=dt, record_every=4)
+    g = O.Grid(N)
+    uh = _shear(g, 1, amp=0.7)
+    ph = np.zeros(g.shape_hat, dtype=complex)
+    u1, ph1, recs, _, _ = O.run(p, n, uh=uh.copy(), ph=ph)
+    assert np.abs(u1 - uh).max() < 1e-13 * np.abs(uh).max()
+    z = -nu * dt
+    rate = nu if integ == O.INTEG_IFRK4 else -math.log(1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24) / dt
+    assert recs[0]["A"] == 0.0  # before the first step
+    for r in recs[1:]:
+        assert abs(r["A"] - rate) < 1e-10 * rate
+        assert abs(r["P_inj"] - 2.0 * nu * r["E_forced"]) < 1e-6 * r["P_inj"] * (integ == O.INTEG_RK4) + 1e-10 * r["P_inj"]
+
+
+def test_hold_forcing_rescales_only_the_band():
+    # one step of a turbulent state: the band energy returns to its starting
+    # value, and every mode outside the band is exactly the unforced step's
+    N = 24
+    g = O.Grid(N)
+    p = O.Params(N=N, nu=0.02, forcing=O.FORCE_HOLD_ENERGY, kF=2.0, ic=O.IC_SPECTRUM_K4, seed=7, dt=0.004)
+    uh, ph = O.init_field(g, p)
+    ef0 = O.forced_energy(uh, g, p.kF)
+    free = O.Params(**{**p.__dict__, "forcing": O.FORCE_NONE})
+    uf, pf = O.step(uh, ph, g, free, p.dt)
+    u1, ph1, _, _, _ = O.run(p, 1, uh=uh.copy(), ph=ph.copy(), with_records=False)
+    assert abs(O.forced_energy(u1, g, p.kF) - ef0) < 1e-13 * ef0
+    b = O.band(g, p.kF)
+    assert np.array_equal(np.where(b, 0, u1), np.where(b, 0, uf))
+    assert np.array_equal(ph1, pf)
+    # and the band itself is the unforced band times one real factor
+    f = math.sqrt(ef0 / O.forced_energy(uf, g, p.kF))
+    assert np.abs(np.where(b, u1 - f * uf, 0)).max() < 1e-14 * np.abs(uf).max()
+
+
 @pytest.mark.parametrize("Sc", [1.0, 0.1])
 def test_mean_gradient_scalar_closed_form(Sc):
     # u = (0, a sin kx, 0), phi0 = 0: u.grad phi = 0 and u x omega is a gradient,
