@@ -51,7 +51,13 @@ typedef enum {
 
 typedef enum { PSC_FP64 = 0, PSC_FP32_MIXED = 1 } psc_precision;
 typedef enum { PSC_IC_SPECTRUM_K4 = 0, PSC_IC_TAYLOR_GREEN_NOISE = 1, PSC_IC_PAPER_EQ9 = 2 } psc_ic;
-typedef enum { PSC_FORCE_NONE = 0, PSC_FORCE_CONST_POWER = 1 } psc_forcing;
+/* Forcing of the band 0 < |k| <= kF (section 2.3).  CONST_POWER adds A u with
+ * A = eps_inj / (2 E_f) at every RK stage.  HOLD_ENERGY is the paper's
+ * deterministic scheme, applied after the last stage: the band is rescaled so
+ * that it keeps the energy it had at the first step after psc_init_field or
+ * psc_set_state (eps_inj unused); records report the equivalent rate
+ * A = ln(factor) / dt. */
+typedef enum { PSC_FORCE_NONE = 0, PSC_FORCE_CONST_POWER = 1, PSC_FORCE_HOLD_ENERGY = 2 } psc_forcing;
 typedef enum { PSC_INTEG_IFRK4 = 0, PSC_INTEG_RK4 = 1 } psc_integrator;
 
 /* Problem statement (Table 2 of the paper; Sc and beta from section 2.3).

@@ -50,7 +50,7 @@ class CStats(ct.Structure):
 PSC_OK, PSC_EINVAL, PSC_ENOMEM_BUDGET, PSC_ECUDA, PSC_EUNSTABLE, PSC_ETIMEOUT, PSC_EUNSUPPORTED_N = range(7)
 FP64, FP32_MIXED = 0, 1
 IC_SPECTRUM_K4, IC_TAYLOR_GREEN_NOISE, IC_PAPER_EQ9 = 0, 1, 2
-FORCE_NONE, FORCE_CONST_POWER = 0, 1
+FORCE_NONE, FORCE_CONST_POWER, FORCE_HOLD_ENERGY = 0, 1, 2
 INTEG_IFRK4, INTEG_RK4 = 0, 1
 
 # every entry point of include/psc.h: (name, restype, argtypes)

@@ -198,7 +198,8 @@ static psc_status check_params(const psc_params* p) {
   if (!(p->nu >= 0.0) || !(p->Sc > 0.0)) return fail(PSC_EINVAL, "nu must be >= 0 and Sc > 0");
   if (p->cfl <= 0.0 && !(p->dt > 0.0)) return fail(PSC_EINVAL, "dt must be > 0 when cfl <= 0");
   if (p->record_every < 1) return fail(PSC_EINVAL, "record_every must be >= 1");
-  if (p->forcing != PSC_FORCE_NONE && p->forcing != PSC_FORCE_CONST_POWER) return fail(PSC_EINVAL, "bad forcing");
+  if (p->forcing != PSC_FORCE_NONE && p->forcing != PSC_FORCE_CONST_POWER && p->forcing != PSC_FORCE_HOLD_ENERGY)
+    return fail(PSC_EINVAL, "bad forcing");
   if (p->integrator != PSC_INTEG_IFRK4 && p->integrator != PSC_INTEG_RK4) return fail(PSC_EINVAL, "bad integrator");
   if (p->ic < 0 || p->ic > 2) return fail(PSC_EINVAL, "bad ic");
   if (!(p->kF >= 0.0) || !(p->eps_inj >= 0.0)) return fail(PSC_EINVAL, "kF and eps_inj must be >= 0");
@@ -265,6 +266,7 @@ psc_status psc_create(const psc_params* p, void* dev_ws, size_t ws_bytes, void* 
   Ctrl c0;
   std::memset(&c0, 0, sizeof(c0));
   c0.dt = p->dt;
+  c0.Ef0 = -1.0;
   cudaError_t e;
   if (sim->fp64) e = cudaMemcpyAsync(sim->ws + L.tw, twd.data(), twd.size() * 8, cudaMemcpyHostToDevice, sim->st);
   else e = cudaMemcpyAsync(sim->ws + L.tw, twf.data(), twf.size() * 4, cudaMemcpyHostToDevice, sim->st);
@@ -377,9 +379,10 @@ PassArgs pass_args(psc_sim* s, const void* in) {
 }
 
 template <typename T>
-void launch_famp(psc_sim* s, const void* in) {
+void launch_famp(psc_sim* s, const void* in, bool step_start = false) {
   launch(s, PSC_K_FORCING, 1, [&] {
-    k_famp<T><<<1, 32, 0, s->st>>>(s->d, in, s->ctrl, s->p.kF * s->p.kF, s->p.eps_inj, s->p.forcing);
+    k_famp<T><<<1, 32, 0, s->st>>>(s->d, in, s->ctrl, s->p.kF * s->p.kF, s->p.eps_inj, s->p.forcing,
+                                   step_start ? 1 : 0);
   });
 }
 
@@ -433,11 +436,11 @@ void launch_combine(psc_sim* s, int stage, const CombineArgs& c) {
 // The five FFT passes of one RHS evaluation of `in`, leaving the unprojected
 // compact (NL, u.grad phi) in the z region.
 template <typename T>
-void rhs_passes(psc_sim* s, const void* in, bool umax) {
+void rhs_passes(psc_sim* s, const void* in, bool umax, bool step_start = false) {
   PassArgs a = pass_args(s, in);
   a.want_umax = umax ? 1 : 0;
   if (umax) cudaMemsetAsync(&s->ctrl->umax_bits, 0, sizeof(unsigned long long), s->st);
-  launch_famp<T>(s, in);
+  launch_famp<T>(s, in, step_start);
   launch(s, PSC_K_ZINV, 1, [&] { s->tb->zinv(a, false, s->wv[SP_ZINV]); });
   launch(s, PSC_K_YINV, 1, [&] { s->tb->yinv(a, false, s->wv[SP_YINV]); });
   launch(s, PSC_K_XPASS, 1, [&] { s->tb->xpass(a, XMODE_RHS); });
@@ -461,8 +464,13 @@ psc_status do_step(psc_sim* s, int nsteps) {
     const bool reset_dt = s->p.cfl > 0.0;
     for (int stage = 1; stage <= 4; ++stage) {
       const void* vin = stage == 1 ? (const void*)U : (const void*)V;
-      rhs_passes<T>(s, vin, stage == 1 && reset_dt);
+      rhs_passes<T>(s, vin, stage == 1 && reset_dt, stage == 1);
       launch_combine<T>(s, stage, combine_args(s, vin));
+    }
+    if (s->p.forcing == PSC_FORCE_HOLD_ENERGY) {
+      launch(s, PSC_K_FORCING, 1, [&] {
+        k_hold<T><<<1, 32, 0, s->st>>>(s->d, U, s->ctrl, s->p.kF * s->p.kF);
+      });
     }
     PSC_LAUNCHED("psc_step");
     ++s->step;
@@ -500,6 +508,7 @@ psc_status do_init(psc_sim* s) {
   Ctrl c0;
   std::memset(&c0, 0, sizeof(c0));
   c0.dt = s->p.dt;
+  c0.Ef0 = -1.0;
   PSC_CUDA(cudaMemcpyAsync(s->ctrl, &c0, sizeof(c0), cudaMemcpyHostToDevice, s->st));
   launch_iftab<T>(s);
   PSC_LAUNCHED("psc_init_field");
@@ -732,6 +741,10 @@ psc_status psc_set_state(psc_sim* s, const void* src, size_t bytes) {
   psc_state_bytes(s, &nb);
   if (bytes != nb) return fail(PSC_EINVAL, "state size mismatch");
   PSC_CUDA(cudaMemcpyAsync(s->ws + s->L.U, src, nb, cudaMemcpyDefault, s->st));
+  // the deterministic forcing holds the band energy of the state it starts from
+  const double unset[2] = {0.0, -1.0};  // A, Ef0
+  PSC_CUDA(cudaMemcpyAsync(&s->ctrl->A, &unset[0], sizeof(double), cudaMemcpyHostToDevice, s->st));
+  PSC_CUDA(cudaMemcpyAsync(&s->ctrl->Ef0, &unset[1], sizeof(double), cudaMemcpyHostToDevice, s->st));
   PSC_CUDA(cudaStreamSynchronize(s->st));
   return PSC_OK;
 }

@@ -47,6 +47,8 @@ struct Ctrl {
   int pad;
   double moments[NQ];
   long long step;                 // RK4 steps taken (advanced by the last stage of each step)
+  double Ef0;                     // band energy held by the deterministic forcing (< 0: not yet set)
+  double Ef_start;                // band energy of the state at the start of the current step
 };
 
 // Streams of the intermediate buffers (indices into zb / yb).

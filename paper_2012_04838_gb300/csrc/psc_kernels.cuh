@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256) k_combine(CombineArgs c) {
   }
   // the stage input is needed in full only on the forcing band and for the
   // explicit linear terms of plain RK4; elsewhere only u2 (scalar source)
-  const bool band = c.forcing && k2 > 0 && k2 <= c.kF2_floor;
+  const bool band = c.forcing == 1 && k2 > 0 && k2 <= c.kF2_floor;  // in-stage (constant power) only
   const bool all = band || c.integrator == 1;
   const C zero = mk(T(0), T(0));
   const C v1 = vin[S + i];
@@ -141,7 +141,8 @@ __global__ void __launch_bounds__(256) k_combine(CombineArgs c) {
 // Band energy E_f = sum_{0<|k|^2<=kF^2} w |u_k|^2 / (2 N^6) of the state `in`
 // in a fixed order (one thread), and A = eps_inj / (2 E_f) (0 if E_f = 0).
 template <typename T>
-__global__ void k_famp(Dims d, const void* in_, Ctrl* ctrl, double kF2, double eps_inj, int forcing) {
+__global__ void k_famp(Dims d, const void* in_, Ctrl* ctrl, double kF2, double eps_inj, int forcing,
+                       int step_start) {
   using C = typename CT<T>::type;
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const C* in = static_cast<const C*>(in_);
@@ -164,7 +165,53 @@ __global__ void k_famp(Dims d, const void* in_, Ctrl* ctrl, double kF2, double e
   const double n3 = (double)d.N * d.N * d.N;
   const double ef = s / (2.0 * n3 * n3);
   ctrl->Ef = ef;
-  ctrl->A = (forcing == 1 && ef > 1e-300) ? eps_inj / (2.0 * ef) : 0.0;
+  if (step_start) ctrl->Ef_start = ef;
+  // the deterministic forcing keeps the rate of its last rescaling in A
+  if (forcing != 2) ctrl->A = (forcing == 1 && ef > 1e-300) ? eps_inj / (2.0 * ef) : 0.0;
+}
+
+// The paper's deterministic forcing (section 2.3), after the last stage of a
+// step: the band 0 < |k|^2 <= kF^2 of the new state is multiplied by
+// f = sqrt(Ef0 / E_f) so that it keeps the energy Ef0 it had at the start of
+// the first step (Ef0 < 0: the target is taken from this step's start).  A
+// records the equivalent rate ln(f) / dt.  One thread, fixed order.
+template <typename T>
+__global__ void k_hold(Dims d, void* u_, Ctrl* ctrl, double kF2) {
+  using C = typename CT<T>::type;
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  C* u = static_cast<C*>(u_);
+  int kb = 0;
+  while ((double)(kb + 1) * (kb + 1) <= kF2) ++kb;
+  if (kb > d.K) kb = d.K;
+  auto for_band = [&](auto&& fn) {
+    for (int kz = -kb; kz <= kb; ++kz)
+      for (int ky = -kb; ky <= kb; ++ky)
+        for (int kx = 0; kx <= kb; ++kx) {
+          const int k2 = kx * kx + ky * ky + kz * kz;
+          if (k2 == 0 || (double)k2 > kF2) continue;
+          fn(((long long)(kz + d.K) * d.P + (ky + d.K)) * d.M + kx, kx == 0 ? 1.0 : 2.0);
+        }
+  };
+  double s = 0.0;
+  for_band([&](long long i, double w) {
+    for (int f = 0; f < 3; ++f) {
+      const C v = u[f * d.S + i];
+      s += w * ((double)v.x * (double)v.x + (double)v.y * (double)v.y);
+    }
+  });
+  const double n3 = (double)d.N * d.N * d.N;
+  const double ef = s / (2.0 * n3 * n3);
+  double ef0 = ctrl->Ef0;
+  if (ef0 < 0.0) {
+    ef0 = ctrl->Ef_start;
+    ctrl->Ef0 = ef0;
+  }
+  const double f = ef > 1e-300 ? sqrt(ef0 / ef) : 1.0;
+  for_band([&](long long i, double) {
+    for (int c = 0; c < 3; ++c) u[c * d.S + i] = cscale(u[c * d.S + i], (T)f);
+  });
+  ctrl->A = log(f) / ctrl->dt;
+  ctrl->Ef = ef * f * f;
 }
 
 // Integrating factors per axis: e(k) = exp(-nu k^2 dt / 2) (and with D), so

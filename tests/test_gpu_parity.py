@@ -197,6 +197,46 @@ def test_config_c1_full_run_matches_oracle(dev, prec):
 
 
 @pytest.mark.parametrize("prec", PREC, ids=PNAME.get)
+@pytest.mark.parametrize("integ", [B.INTEG_IFRK4, B.INTEG_RK4])
+def test_hold_energy_forcing_matches_oracle(dev, prec, integ):
+    """The paper's deterministic forcing: the band 0 < |k| <= 2 is rescaled
+    after every step to the energy it had at the first step."""
+    N = 32
+    p = B.Params(N=N, precision=prec, integrator=integ, nu=0.02, dt=0.005, forcing=B.FORCE_HOLD_ENERGY,
+                 kF=2.0, ic=B.IC_TAYLOR_GREEN_NOISE, seed=1, record_every=10)
+    sim = B.Simulation(p, device=dev)
+    sim.init_field()
+    got = []
+    for n in (0, 10, 20):
+        if n:
+            sim.step(10)
+        got.append(sim.stats()[0])
+    final = sim.get_state().cpu().numpy().astype(np.complex128)
+    uh, ph, recs, _, _ = O.run(oparams(p), 20, with_records=True)
+    ref = full_to_compact(np.concatenate([uh, ph[None]]), N)
+    assert rel(final, ref) < TOL_TRAJ[prec]
+    tol = 1e-10 if prec == B.FP64 else 1e-4
+    # A = ln(f)/dt with f - 1 ~ A dt: a relative error e of the band energy
+    # moves A by about e/(2 dt), so FP32-mixed gets an absolute allowance
+    atol_A = 0.0 if prec == B.FP64 else 1e-6 / p.dt
+    for rec, r in zip(got, recs):
+        assert abs(rec["E_forced"] - r["E_forced"]) <= tol * r["E_forced"]
+        assert abs(rec["A"] - r["A"]) <= tol * abs(r["A"]) + atol_A, (rec["step"], rec["A"], r["A"])
+    assert got[0]["A"] == 0.0 and got[2]["A"] != 0.0
+    # the band energy is held at its starting value
+    assert abs(got[2]["E_forced"] - got[0]["E_forced"]) <= (1e-12 if prec == B.FP64 else 1e-6) * got[0]["E_forced"]
+    # a state set from outside becomes the new target
+    x = as_input(random_compact_state(N, 77, kpeak=3.0), prec)
+    sim.set_state(torch.from_numpy(x).to(dev))
+    sim.step(5)
+    got = sim.get_state().cpu().numpy().astype(np.complex128)
+    f = compact_to_full(x, N)
+    uh, ph, _, _, _ = O.run(oparams(p), 5, uh=f[:3], ph=f[3], with_records=False)
+    assert rel(got, full_to_compact(np.concatenate([uh, ph[None]]), N)) < TOL_TRAJ[prec]
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", PREC, ids=PNAME.get)
 def test_cfl_controlled_run_matches_oracle(dev, prec):
     N = 32
     p = B.Params(N=N, precision=prec, nu=0.01, cfl=0.5, record_every=5, ic=B.IC_SPECTRUM_K4,
