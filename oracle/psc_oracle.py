@@ -191,6 +191,22 @@ def nonlinear_convective(uh, g: Grid):
     return project(out, g)
 
 
+def pressure_hat(uh, g: Grid):
+    """The modified pressure of section 2.2 on R: taking the divergence of the
+    momentum equation gives p_hat = i k.(u.grad u)_hat / |k|^2 (Eq. 6), with
+    the convective term formed as the paper forms it (u and i k u_hat
+    transformed back separately) and truncated to R; the forcing term drops
+    out because A u is solenoidal.  p_hat = 0 at k = 0."""
+    u = velocity(uh, g)
+    adv = []
+    for i in range(3):
+        gi = [inv(c, g.N) for c in grad_hat(uh[i], g)]
+        adv.append(truncate(fwd(u[0] * gi[0] + u[1] * gi[1] + u[2] * gi[2]), g))
+    kdot = sum(kc * a for kc, a in zip(g.kvec, adv))
+    k2 = np.where(g.k2 == 0, 1, g.k2)
+    return np.where(g.k2 == 0, 0.0, 1j * kdot / k2)
+
+
 def scalar_advection(uh, ph, g: Grid):
     """(u.grad phi)_hat on R (Eq. 8), formed in physical space from the
     inverse transforms of u_hat and i k phi_hat."""

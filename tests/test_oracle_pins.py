@@ -133,6 +133,39 @@ def test_rotational_equals_convective_form():
     assert max(np.abs(x - y).max() for x, y in zip(a, b)) < 1e-11 * scale
 
 
+@pytest.mark.parametrize("N", [8, 16])
+def test_taylor_green_pressure_closed_form(N):
+    # u = (sin x cos y cos z, -cos x sin y cos z, 0) has the pressure
+    # p = (cos 2x + cos 2y)(cos 2z + 2)/16 up to a constant (from -lap p =
+    # d_i u_j d_j u_i); all its modes have |k_i| <= 2 <= K, so it is exact on R
+    g = O.Grid(N)
+    x, y, z = g.x, g.y, g.z
+    u = np.sin(x) * np.cos(y) * np.cos(z)
+    v = -np.cos(x) * np.sin(y) * np.cos(z)
+    uh = np.array([O.fwd(np.broadcast_to(u, (N,) * 3)), O.fwd(np.broadcast_to(v, (N,) * 3)),
+                   O.fwd(np.zeros((N,) * 3))])
+    p = O.inv(O.pressure_hat(uh, g), N)
+    exact = (np.cos(2 * x) + np.cos(2 * y)) * (np.cos(2 * z) + 2) / 16.0
+    exact = np.broadcast_to(exact - exact.mean(), (N,) * 3)
+    assert np.abs(p - exact).max() < 1e-14
+
+
+def test_pressure_balances_the_projection():
+    # the projection removes exactly the pressure gradient:
+    # -(u.grad u)_hat - i k p_hat is solenoidal and equals P[-(u.grad u)_hat]
+    g, uh, _ = _rand_velocity(16, 3)
+    p = O.pressure_hat(uh, g)
+    conv = O.nonlinear_convective(uh, g)  # -P[(u.grad u)_hat]
+    u = O.velocity(uh, g)
+    raw = []
+    for i in range(3):
+        gi = [O.inv(c, g.N) for c in O.grad_hat(uh[i], g)]
+        raw.append(-O.truncate(O.fwd(u[0] * gi[0] + u[1] * gi[1] + u[2] * gi[2]), g))
+    rebuilt = [raw[c] - 1j * g.kvec[c] * p for c in range(3)]
+    scale = max(np.abs(c).max() for c in conv)
+    assert max(np.abs(a - b).max() for a, b in zip(rebuilt, conv)) < 1e-12 * scale
+
+
 def test_nonlinear_terms_conserve_energy_and_variance():
     # sum_k Re(u* . N(u)) = 0 and sum_k Re(phi* . (u.grad phi)) = 0 on the
     # Galerkin-truncated system (3K < N makes the grid sums exact).
