@@ -147,6 +147,14 @@ psc_status psc_set_state(psc_sim* s, const void* src, size_t bytes);
  * Asynchronous on the stream. */
 psc_status psc_rhs(psc_sim* s, const void* in, void* out);
 
+/* The modified pressure of the current state (section 2.2, Eq. 6):
+ * p_k = i k.(u.grad u)_k / |k|^2 on the retained set, p_0 = 0, written to the
+ * device pointer `out` as one compact field ((2K+1)^2 (K+1) complex values in
+ * the state's precision, layout [kz+K][ky+K][kx]; `bytes` must be that size;
+ * `out` must not overlap the workspace).  Computed as -i k.(u x omega)_k/|k|^2
+ * - (|u|^2/2)_k.  Asynchronous on the stream. */
+psc_status psc_pressure(psc_sim* s, void* out, size_t bytes);
+
 /* Time, step counter and current dt (host values; synchronises). */
 psc_status psc_time(psc_sim* s, double* t, int64_t* step, double* dt);
 

@@ -76,6 +76,7 @@ EXPORTS = [
     ("psc_launch_count", ct.c_int, [_VP, ct.POINTER(ct.c_int64)]),
     ("psc_tile_widths", ct.c_int, [_VP, ct.POINTER(ct.c_int32)]),
     ("psc_tile_staged", ct.c_int, [_VP, ct.POINTER(ct.c_int32)]),
+    ("psc_pressure", ct.c_int, [_VP, _VP, ct.c_size_t]),
     ("psc_destroy", ct.c_int, [_VP]),
     ("psc_shell_spectra_noalloc", ct.c_int, [_VP, ct.c_int32, ct.c_int32, ct.POINTER(ct.c_double),
                                              ct.POINTER(ct.c_double), ct.c_int32, _VP]),
@@ -244,6 +245,16 @@ class Simulation:
         x = state.to(device=self.device, dtype=self.cdtype).contiguous()
         out = self.torch.empty_like(x)
         _check(self.lib, self.lib.psc_rhs(self._h, ct.c_void_p(x.data_ptr()), ct.c_void_p(out.data_ptr())))
+        self.stream.synchronize()
+        return out
+
+    def pressure(self):
+        """Modified pressure p_hat of the current state (Eq. 6), one compact
+        field as a new device tensor [2K+1][2K+1][K+1]."""
+        K = (self.p.N - 1) // 3
+        out = self.torch.empty((2 * K + 1, 2 * K + 1, K + 1), dtype=self.cdtype, device=self.device)
+        _check(self.lib, self.lib.psc_pressure(self._h, ct.c_void_p(out.data_ptr()),
+                                               out.numel() * out.element_size()))
         self.stream.synchronize()
         return out
 

@@ -489,6 +489,21 @@ psc_status do_rhs(psc_sim* s, const void* in, void* out) {
 }
 
 template <typename T>
+psc_status do_pressure(psc_sim* s, void* out) {
+  const void* U = s->ws + s->L.U;
+  PassArgs a = pass_args(s, U);
+  launch(s, PSC_K_ZINV, 1, [&] { s->tb->zinv(a, false, s->wv[SP_ZINV]); });
+  launch(s, PSC_K_YINV, 1, [&] { s->tb->yinv(a, false, s->wv[SP_YINV]); });
+  launch(s, PSC_K_XPASS, 1, [&] { s->tb->xpass(a, XMODE_PRESSURE); });
+  launch(s, PSC_K_YFWD, 1, [&] { s->tb->yfwd(a, s->wv[SP_YFWD]); });
+  launch(s, PSC_K_ZFWD, 1, [&] { s->tb->zfwd(a, s->wv[SP_ZFWD]); });
+  const int blocks = (int)((s->d.S + 255) / 256);
+  launch(s, PSC_K_OTHER, 1, [&] { k_pressure<T><<<blocks, 256, 0, s->st>>>(s->d, a.rb, out); });
+  PSC_LAUNCHED("psc_pressure");
+  return PSC_OK;
+}
+
+template <typename T>
 psc_status do_init(psc_sim* s) {
   const Dims& d = s->d;
   double2* z = (double2*)(s->ws + s->L.yreg);
@@ -715,6 +730,12 @@ psc_status psc_step(psc_sim* s, int32_t nsteps) {
 psc_status psc_rhs(psc_sim* s, const void* in, void* out) {
   if (!s || !in || !out) return fail(PSC_EINVAL, "null argument");
   return s->fp64 ? do_rhs<double>(s, in, out) : do_rhs<float>(s, in, out);
+}
+
+psc_status psc_pressure(psc_sim* s, void* out, size_t bytes) {
+  if (!s || !out) return fail(PSC_EINVAL, "null argument");
+  if (bytes != (size_t)s->d.S * (s->fp64 ? 16 : 8)) return fail(PSC_EINVAL, "pressure buffer size mismatch");
+  return s->fp64 ? do_pressure<double>(s, out) : do_pressure<float>(s, out);
 }
 
 psc_status psc_spectra_and_stats(psc_sim* s, double* Ek, double* Ephi, int32_t cap, int32_t* nshell,

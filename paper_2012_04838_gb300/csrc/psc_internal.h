@@ -70,7 +70,9 @@ struct PassArgs {
   cudaStream_t st;
 };
 
-enum { XMODE_RHS = 0, XMODE_STATS = 1 };
+// X-pass modes: the right-hand side (u x omega, u . grad phi); the statistics
+// moments; the pressure inputs (u x omega and |u|^2/2 in place of the scalar term)
+enum { XMODE_RHS = 0, XMODE_STATS = 1, XMODE_PRESSURE = 2 };
 
 // Strided passes come in tile-width variants v (index into widths[]).
 enum { SP_ZINV = 0, SP_YINV = 1, SP_YFWD = 2, SP_ZFWD = 3, SP_N = 4 };

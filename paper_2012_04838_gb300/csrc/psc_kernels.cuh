@@ -138,6 +138,32 @@ __global__ void __launch_bounds__(256) k_combine(CombineArgs c) {
   }
 }
 
+// Modified pressure (section 2.2, Eq. 6) from the transformed pressure inputs
+// r = (u x omega, |u|^2/2) on the retained set: with u.grad u = -u x omega +
+// grad(|u|^2/2), p_hat = i k.(u.grad u)_hat/|k|^2 = -i k.(u x omega)_hat/|k|^2
+// - (|u|^2/2)_hat; p_hat = 0 at k = 0.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pressure(Dims d, const void* rb_, void* out_) {
+  using C = typename CT<T>::type;
+  const long long S = d.S;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S) return;
+  int kx, ky, kz;
+  mode_of(d, i, kx, ky, kz);
+  const int k2 = kx * kx + ky * ky + kz * kz;
+  const C* r = static_cast<const C*>(rb_);
+  C* out = static_cast<C*>(out_);
+  if (k2 == 0) {
+    out[i] = mk(T(0), T(0));
+    return;
+  }
+  const C a = r[i], b = r[S + i], c = r[2 * S + i], q = r[3 * S + i];
+  const T ik2 = T(1) / T(k2);
+  const C kdot = mk(kx * a.x + ky * b.x + kz * c.x, kx * a.y + ky * b.y + kz * c.y);
+  // -i (k.NL) / |k|^2 - q
+  out[i] = mk(kdot.y * ik2 - q.x, -kdot.x * ik2 - q.y);
+}
+
 // Band energy E_f = sum_{0<|k|^2<=kF^2} w |u_k|^2 / (2 N^6) of the state `in`
 // in a fixed order (one thread), and A = eps_inj / (2 E_f) (0 if E_f = 0).
 template <typename T>

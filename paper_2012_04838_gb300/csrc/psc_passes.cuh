@@ -522,7 +522,7 @@ k_xpass(PassArgs a) {
     auto pos = [&](int j, int k2) { return (t + j * TPL) + R1 * k2; };
     C z[J2][R2];
 
-    if constexpr (MODE == XMODE_RHS) {
+    if constexpr (MODE == XMODE_RHS || MODE == XMODE_PRESSURE) {
       T ux[J2][R2], uy[J2][R2], uz[J2][R2];
       T nlx[J2][R2], nly[J2][R2], nlz[J2][R2], sv[J2][R2];
       auto getu = [&](int c, int j, int k2) -> T {
@@ -588,6 +588,27 @@ k_xpass(PassArgs a) {
                    }
                  },
                  ex, tw, t);
+      if constexpr (MODE == XMODE_PRESSURE) {
+        // (NL3, |u|^2 / 2): the inputs of the modified pressure
+#pragma unroll
+        for (int j = 0; j < J2; ++j)
+#pragma unroll
+          for (int k2 = 0; k2 < R2; ++k2) {
+            const T u1 = getu(0, j, k2), u2 = getu(1, j, k2), u3 = getu(2, j, k2);
+            z[j][k2] = mk(nlz[j][k2], T(0.5) * (u1 * u1 + u2 * u2 + u3 * u3));
+          }
+        xfwd<T, N>(z,
+                   [&](int kx, C X1, C X2) {
+                     if (!valid) return;
+                     const long long i0 = line * M + kx;
+                     if (PSC_OK_INDEX(i0 + 3 * ys, 4 * ys, a.ctrl)) {
+                       xb[2 * ys + i0] = X1;
+                       xb[3 * ys + i0] = X2;
+                     }
+                   },
+                   ex, tw, t);
+        continue;
+      }
       // (dphi/dx1, dphi/dx2)
       xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_PHI, kx), T(kx)); x2 = Y(Y_DYPHI, kx); },
                  z, ex, tw, t, scale);
@@ -877,6 +898,18 @@ template <typename T, int N> struct Passes {
     return n[dev];
   }
   static void xpass(const PassArgs& a, int mode) {
+    if (mode == XMODE_PRESSURE) {
+      if constexpr (X2) {
+        const size_t sm2 = X2Cfg<T, N>::SMEM;
+        prep(k_xpass2<T, N, XMODE_PRESSURE>, sm2);
+        k_xpass2<T, N, XMODE_PRESSURE><<<xgrid(), 128, sm2, a.st>>>(a);
+      } else {
+        const size_t sm = XCfg<T, N>::SMEM;
+        prep(k_xpass<T, N, XMODE_PRESSURE>, sm);
+        k_xpass<T, N, XMODE_PRESSURE><<<xgrid(), dim3(32 * XCfg<T, N>::WARPS), sm, a.st>>>(a);
+      }
+      return;
+    }
     if constexpr (X2S) {
       if (mode == XMODE_RHS) {
         using SC = X2SCfg<T, N>;

@@ -233,7 +233,7 @@ __device__ __forceinline__ void x2_twiddles(typename CT<T>::type* t1, const type
 // Y(s, kx) reads stream s at kx.  after_a() runs once streams UX..DYUX are no
 // longer read, wait_b() before PHI..DZPHI are first read (false aborts the
 // row), after_b() once those are no longer read.  Returns false if aborted.
-template <typename T, int N, class YF, class HA, class WB, class HB>
+template <typename T, int N, bool PRESSURE = false, class YF, class HA, class WB, class HB>
 __device__ __forceinline__ bool x2_rhs_row(const YF& Y, const HA& after_a, const WB& wait_b, const HB& after_b,
                                            typename CT<T>::type* __restrict__ xb, long long line, long long ys,
                                            typename CT<T>::type* ex, const X2Roles<typename CT<T>::type>& q,
@@ -280,6 +280,19 @@ __device__ __forceinline__ bool x2_rhs_row(const YF& Y, const HA& after_a, const
                 if (PSC_OK_INDEX(i0 + ys, 4 * ys, ctrl)) { xb[i0] = X1; xb[i0 + ys] = X2; }
               },
               ex, q);
+  if constexpr (PRESSURE) {
+    // (NL3, |u|^2 / 2): the inputs of the modified pressure
+#pragma unroll
+    for (int b = 0; b < 16; ++b)
+      z[b] = mk(W[b] * s2, T(0.5) * (u1[b] * u1[b] + u2[b] * u2[b] + u3[b] * u3[b]) * s2);
+    x2fwd<T, N>(z,
+                [&](int kx, C X1, C X2) {
+                  const long long i0 = 2 * ys + line * M + kx;
+                  if (PSC_OK_INDEX(i0 + ys, 4 * ys, ctrl)) { xb[i0] = X1; xb[i0 + ys] = X2; }
+                },
+                ex, q);
+    return true;
+  }
   if (!wait_b()) return false;
   // (dphi/dx1, dphi/dx2); u1 then holds the partial u . grad phi
   x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_PHI, kx), T(kx)); x2 = Y(Y_DYPHI, kx); },
@@ -348,8 +361,9 @@ __global__ void __launch_bounds__(128, PSC_X2_MINB) k_xpass2(PassArgs a) {
       return row[s * ys + kx];
     };
     C z[16];
-    if constexpr (MODE == XMODE_RHS) {
-      x2_rhs_row<T, N>(Y, [] {}, [] { return true; }, [] {}, xb, line, ys, ex, q, scale, a.want_umax != 0,
+    if constexpr (MODE == XMODE_RHS || MODE == XMODE_PRESSURE) {
+      x2_rhs_row<T, N, MODE == XMODE_PRESSURE>(Y, [] {}, [] { return true; }, [] {}, xb, line, ys, ex, q, scale,
+                       a.want_umax != 0,
                        um, a.ctrl);
     } else {
       // statistics (Eqs. 11-13): per pair, partial sums of the thread's 16

@@ -330,3 +330,51 @@ def test_nonfinite_state_is_reported_unstable(dev, prec):
     ok.step(1)
     rec, _, _ = ok.stats()
     assert np.isfinite(rec["K"])
+
+
+# ---------------------------------------------------------------- pressure
+
+@pytest.mark.parametrize("prec", PREC, ids=PNAME.get)
+@pytest.mark.parametrize("N", [16, 32, 48, 96])
+def test_pressure_matches_oracle(dev, N, prec):
+    p = B.Params(N=N, precision=prec)
+    sim = B.Simulation(p, device=dev)
+    x = as_input(random_compact_state(N, 500 + N), prec)
+    sim.set_state(torch.from_numpy(x).to(dev))
+    got = sim.pressure().cpu().numpy().astype(np.complex128)
+    f = compact_to_full(x, N)
+    ref = full_to_compact(O.pressure_hat(f[:3], O.Grid(N))[None], N)[0]
+    assert rel(got, ref) < TOL_RHS[prec]
+    sim.close()
+
+
+def _embed(small, n1, n2):
+    """A compact state of an n1 grid as the same physical field on an n2 grid
+    (unnormalised coefficients scale with N^3)."""
+    k1, k2 = (n1 - 1) // 3, (n2 - 1) // 3
+    big = np.zeros((small.shape[0], 2 * k2 + 1, 2 * k2 + 1, k2 + 1), dtype=small.dtype)
+    big[:, k2 - k1:k2 + k1 + 1, k2 - k1:k2 + k1 + 1, :k1 + 1] = small * (n2 / n1) ** 3
+    return big
+
+
+@pytest.mark.parametrize("N", [512, 1024])
+def test_pressure_of_taylor_green_at_full_size(dev, N):
+    """The Taylor-Green field has the closed-form pressure
+    (cos 2x + cos 2y)(cos 2z + 2)/16 (pinned in the oracle at 16^3); the same
+    field on the large grid must give the same coefficients, and nothing else."""
+    n1 = 16
+    g = O.Grid(n1)
+    u = np.broadcast_to(np.sin(g.x) * np.cos(g.y) * np.cos(g.z), (n1,) * 3)
+    v = np.broadcast_to(-np.cos(g.x) * np.sin(g.y) * np.cos(g.z), (n1,) * 3)
+    uh = np.array([O.fwd(u), O.fwd(v), O.fwd(np.zeros((n1,) * 3))])
+    small = full_to_compact(np.concatenate([uh, np.zeros((1,) + uh.shape[1:], complex)]), n1)
+    ref_small = full_to_compact(O.pressure_hat(uh, g)[None], n1)
+    p = B.Params(N=N, precision=B.FP32_MIXED)
+    sim = B.Simulation(p, device=dev)
+    sim.set_state(torch.from_numpy(_embed(small, n1, N).astype(np.complex64)).to(dev))
+    got = sim.pressure().cpu().numpy().astype(np.complex128)
+    ref = _embed(ref_small, n1, N)[0]
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() < 1e-6 * scale
+    sim.close()
+    torch.cuda.empty_cache()
