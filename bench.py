@@ -533,22 +533,27 @@ def main():
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        sim.set_state(host)
+        sim.set_state(host)  # synchronous
+        t1 = time.perf_counter()
         for i in range(a.steps):
             sim.step(1)
             if i % rec_every == 0:
                 sim.stats()
                 nrec += 1
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
         st = sim.lib.psc_get_state(sim._h, back.data_ptr(), sim.state_bytes())
         if st != 0:
             raise RuntimeError("psc_get_state failed")
-        el = max_over_ranks(time.perf_counter() - t0, world, dev)
+        t3 = time.perf_counter()
+        el = max_over_ranks(t3 - t0, world, dev)
         rec_bytes = 37 * 8 + 2 * 8 * 600
         out["e2e"] = {"value": world * a.steps / el, "unit": "steps/s",
                       "h2d_bytes_per_step": sim.state_bytes() / a.steps,
                       "d2h_bytes_per_step": (sim.state_bytes() + nrec * rec_bytes) / a.steps,
                       "what": "set_state from pinned host memory, steps with records every 10 steps, "
-                              "get_state to pinned host memory"}
+                              "get_state to pinned host memory",
+                      "phases_s": {"h2d": round(t1 - t0, 4), "steps": round(t2 - t1, 4), "d2h": round(t3 - t2, 4)}}
     sim.close()
     del sim
     torch.cuda.empty_cache()

@@ -488,8 +488,13 @@ template <typename T, int N> struct X2SCfg {
   static constexpr int THREADS = XC::TH * ROWS;
   static constexpr int M = XC::K + 1;
   static constexpr int NA = 6, NB = 3;  // streams Y_UX..Y_DYUX, Y_PHI..Y_DZPHI
+#ifndef PSC_X2S_STAGE_B
+#define PSC_X2S_STAGE_B 1
+#endif
+  // stage the scalar streams too (else they are read from global memory)
+  static constexpr bool STAGE_B = PSC_X2S_STAGE_B;
   static constexpr unsigned ROW_BYTES = (unsigned)(M * sizeof(C));
-  static constexpr size_t STAGE_BYTES = (size_t)(NA + NB) * ROW_BYTES;
+  static constexpr size_t STAGE_BYTES = (size_t)(NA + (STAGE_B ? NB : 0)) * ROW_BYTES;
   static constexpr size_t GROUP_BYTES = STAGE_BYTES + XC::LINE_BYTES;
   static constexpr size_t TW_OFF = GROUP_BYTES * ROWS;
   static constexpr size_t BAR_OFF = TW_OFF + XC::TW_BYTES;
@@ -550,9 +555,10 @@ __global__ void __launch_bounds__(X2SCfg<T, N>::THREADS, 1) k_xpass2s(PassArgs a
   if (line < nlines) {
     if (leader) {
       issue(line, 0, SC::NA, barA);
-      issue(line, SC::NA, SC::NA + SC::NB, barB);
+      if constexpr (SC::STAGE_B) issue(line, SC::NA, SC::NA + SC::NB, barB);
     }
-    ia = ib = true;
+    ia = true;
+    ib = SC::STAGE_B;
   }
 #pragma unroll 1
   for (; line < nlines; line += stride) {
@@ -563,7 +569,11 @@ __global__ void __launch_bounds__(X2SCfg<T, N>::THREADS, 1) k_xpass2s(PassArgs a
     if (!ok) break;
     pa ^= 1u;
     ia = false;
-    auto Y = [&](int st, int kx) -> C { return stg[st * M + kx]; };
+    const C* __restrict__ row = yb + line * M;
+    auto Y = [&](int st, int kx) -> C {
+      if (SC::STAGE_B || st < SC::NA) return stg[st * M + kx];
+      return row[st * ys + kx];
+    };
     ok = x2_rhs_row<T, N>(
         Y,
         [&] {
@@ -573,6 +583,7 @@ __global__ void __launch_bounds__(X2SCfg<T, N>::THREADS, 1) k_xpass2s(PassArgs a
           }
         },
         [&] {
+          if constexpr (!SC::STAGE_B) return true;
           const bool w = bar_and(q.bar, TH, leader ? mbar_wait(barB, pb, &a.ctrl->err) : true);
           if (w) {
             pb ^= 1u;
@@ -581,9 +592,11 @@ __global__ void __launch_bounds__(X2SCfg<T, N>::THREADS, 1) k_xpass2s(PassArgs a
           return w;
         },
         [&] {
-          if (next < nlines) {
-            if (leader) issue(next, SC::NA, SC::NA + SC::NB, barB);
-            ib = true;
+          if constexpr (SC::STAGE_B) {
+            if (next < nlines) {
+              if (leader) issue(next, SC::NA, SC::NA + SC::NB, barB);
+              ib = true;
+            }
           }
         },
         xb, line, ys, ex, q, scale, a.want_umax != 0, um, a.ctrl);
