@@ -42,12 +42,22 @@ template <typename T, int N, int W, bool INV> struct StagedTile {
   static constexpr int BOXR = (((ROWS + NBOX - 1) / NBOX) + 1) & ~1;
   static constexpr unsigned BOX_BYTES = (unsigned)(BOXR * W * sizeof(C));
   static constexpr unsigned BYTES = NBOX * BOX_BYTES;
-  // the exchange buffer, then the staging tile (twiddles are read through L1)
-  static constexpr size_t STG_OFF = (StridedSmem<T, N, W>::EXCH_BYTES + 127) / 128 * 128;
-  static constexpr size_t BAR_OFF = STG_OFF + BYTES;
+  // The exchange buffer, then the staging tile, then (TW_SMEM) the step-1
+  // twiddle table.  The table is kept in shared memory when it costs no CTA
+  // per SM; otherwise the twiddles are read through L1
+  static constexpr size_t EXCH = StridedSmem<T, N, W>::EXCH_BYTES;
+  static constexpr size_t TWB = (size_t)N * sizeof(C);
+  static constexpr size_t STG_OFF = (EXCH + 127) / 128 * 128;
+  static constexpr size_t BASE = STG_OFF + BYTES + sizeof(unsigned long long);
+  static constexpr int fit(size_t b) { return (int)((228 * 1024) / (b + 1024)); }
+  // (inverse passes only: measured faster there, slower for the forward ones)
+  static constexpr bool TW_SMEM =
+      INV && BASE + TWB <= 227 * 1024 && (fit(BASE + TWB) >= fit(BASE) || fit(BASE + TWB) >= 4);
+  static constexpr size_t TW_OFF = STG_OFF + BYTES;  // 128-byte aligned
+  static constexpr size_t BAR_OFF = TW_OFF + (TW_SMEM ? TWB : 0);
   static constexpr size_t SMEM = BAR_OFF + sizeof(unsigned long long);
   // CTAs per SM that fit its 228 KB of shared memory (1 KB reserved per CTA)
-  static constexpr int FIT = (int)((228 * 1024) / (SMEM + 1024));
+  static constexpr int FIT = fit(SMEM);
   // no more CTAs than leave every thread 128 registers
   static constexpr int RFIT = 512 / (W * PlanD<N>::TPL) < 1 ? 1 : 512 / (W * PlanD<N>::TPL);
   static constexpr int MINB = FIT < 1 ? 1 : (FIT < RFIT ? FIT : RFIT);
@@ -57,10 +67,11 @@ template <typename T, int N, int W, bool INV> struct StagedTile {
 
 // One length-N DFT per column from step-1 inputs already in registers:
 // in[j][n1] is line position R2 n1 + t + j TPL.  Same steps as strided_fft,
-// with the step-1 twiddles wN^(n2 k1) read from the global table tw.  It does
-// not end with a barrier: the caller's next CTA barrier must come before the
-// exchange buffer is written again.
-template <typename T, int N, int W, int DIR, class ST>
+// with the step-1 twiddles wN^(n2 k1) from the shared table of
+// strided_twiddles (TW_SMEM) or from the global table tw.  It does not end
+// with a barrier: the caller's next CTA barrier must come before the exchange
+// buffer is written again.
+template <typename T, int N, int W, int DIR, bool TW_SMEM, class ST>
 __device__ __forceinline__ void strided_fft_regs(typename CT<T>::type (&in)[PlanD<N>::J1][PlanD<N>::R1],
                                                  const ST& st, typename CT<T>::type* sm,
                                                  const typename CT<T>::type* __restrict__ tw, int t, int w) {
@@ -76,7 +87,8 @@ __device__ __forceinline__ void strided_fft_regs(typename CT<T>::type (&in)[Plan
     for (int k1 = 0; k1 < R1; ++k1) {
       C v = in[j][k1];
       if (k1 > 0) {
-        const C wv = __ldg(&tw[n2 * k1]);  // wN^(n2 k1), n2 k1 < N
+        // wN^(n2 k1), n2 k1 < N
+        const C wv = TW_SMEM ? tw[(j * R1 + k1) * TPL + t] : __ldg(&tw[n2 * k1]);
         v = (DIR < 0) ? cmul(v, wv) : cmulc(v, wv);
       }
       sm[k1 * SM::ROW + n2 * W + w] = v;
@@ -170,8 +182,21 @@ k_strided_s(PassArgs a, const __grid_constant__ CUtensorMap tm) {
     mbar_init(bar, 1);
     mbar_init_fence();
   }
-  const C* __restrict__ tw = static_cast<const C*>(a.tw);
-  __syncthreads();  // barrier initialised before any thread waits on it
+  const C* tw;
+  if constexpr (TL::TW_SMEM) {
+    // the shared table of strided_twiddles, laid out [j][k1][t]
+    C* t1 = reinterpret_cast<C*>(smraw + TL::TW_OFF);
+    const C* __restrict__ g = static_cast<const C*>(a.tw);
+    const int nthr = blockDim.x * blockDim.y, me = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int i = me; i < N; i += nthr) {
+      const int tt = i % TPL, k1 = (i / TPL) % R1, j = i / (TPL * R1);
+      t1[i] = g[(tt + j * TPL) * k1];
+    }
+    tw = t1;
+  } else {
+    tw = static_cast<const C*>(a.tw);
+  }
+  __syncthreads();  // barrier initialised and twiddles in place before use
   const long long S = (long long)P * P * M, zs = (long long)N * P * M, ys = (long long)N * N * M;
   auto issue = [&](int tr) {
     int src, kind, s2, out;
@@ -244,7 +269,7 @@ k_strided_s(PassArgs a, const __grid_constant__ CUtensorMap tm) {
     if (leader && tr + 1 < SPL::NT) issue(tr + 1);
     if constexpr (PASS == SP_ZINV) {
       C* __restrict__ zo = static_cast<C*>(a.zb);
-      strided_fft_regs<T, N, W, +1>(
+      strided_fft_regs<T, N, W, +1, TL::TW_SMEM>(
           in,
           [&](int z, C v) {
             if (!act) return;
@@ -254,7 +279,7 @@ k_strided_s(PassArgs a, const __grid_constant__ CUtensorMap tm) {
           sm, tw, t, w);
     } else if constexpr (PASS == SP_YINV) {
       C* __restrict__ yo = static_cast<C*>(a.yb);
-      strided_fft_regs<T, N, W, +1>(
+      strided_fft_regs<T, N, W, +1, TL::TW_SMEM>(
           in,
           [&](int y, C v) {
             if (!act) return;
@@ -264,7 +289,7 @@ k_strided_s(PassArgs a, const __grid_constant__ CUtensorMap tm) {
           sm, tw, t, w);
     } else if constexpr (PASS == SP_YFWD) {
       C* __restrict__ yo = static_cast<C*>(a.yf);
-      strided_fft_regs<T, N, W, -1>(
+      strided_fft_regs<T, N, W, -1, TL::TW_SMEM>(
           in,
           [&](int k, C v) {
             int ky;
@@ -275,7 +300,7 @@ k_strided_s(PassArgs a, const __grid_constant__ CUtensorMap tm) {
           sm, tw, t, w);
     } else {
       C* __restrict__ ro = static_cast<C*>(a.rb);
-      strided_fft_regs<T, N, W, -1>(
+      strided_fft_regs<T, N, W, -1, TL::TW_SMEM>(
           in,
           [&](int k, C v) {
             int kz;
