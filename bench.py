@@ -529,6 +529,9 @@ def main():
     if not a.no_e2e:
         host = sim.get_state(device="cpu").pin_memory()
         back = torch.empty_like(host).pin_memory()
+        # one untimed round trip through both pinned buffers (first-use costs)
+        sim.set_state(host)
+        sim.lib.psc_get_state(sim._h, back.data_ptr(), sim.state_bytes())
         nrec = 0
         torch.cuda.synchronize()
         barrier()
