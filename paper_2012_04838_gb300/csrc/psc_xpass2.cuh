@@ -324,7 +324,7 @@ template <typename T, int N, int MODE>
 #ifndef PSC_X2_MINB
 #define PSC_X2_MINB 4
 #endif
-__global__ void __launch_bounds__(128, PSC_X2_MINB) k_xpass2(PassArgs a) {
+__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : PSC_X2_MINB) k_xpass2(PassArgs a) {
   using C = typename CT<T>::type;
   using XC = X2Cfg<T, N>;
   constexpr int TH = XC::TH, G = XC::G, ROWS = XC::ROWS, M = XC::K + 1;
