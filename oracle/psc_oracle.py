@@ -17,7 +17,8 @@ x1, x2, x3 directions.
 Readings of the paper that the oracle adopts (the GPU path adopts the same):
   * 2/3-rule truncation: keep ``|k_i| <= K = floor((N-1)/3)`` on every axis.
   * rotational nonlinear term ``P(u x omega)`` (equal to ``-P(u.grad u)`` on
-    the retained set; both forms are implemented and their agreement is a test).
+    the retained set; both forms are implemented, selectable by
+    ``nonlinear_form``, and their agreement is a test).
   * constant-power forcing ``A = eps_inj / (2 E_f)`` on the sphere
     ``0 < |k|^2 <= k_F^2``, evaluated at every stage input; or the paper's
     deterministic variant (section 2.3), applied after the last stage: the
@@ -51,6 +52,9 @@ IC_PAPER_EQ9 = 2            # Eq. 9 shape (k/kF)^2 below kF, (k/kF)^(-5/3) above
 INTEG_IFRK4 = 0
 INTEG_RK4 = 1
 
+NL_ROTATIONAL = 0           # P(u x omega)
+NL_CONVECTIVE = 1           # -P((u.grad) u), the form the paper writes (section 2.3)
+
 
 @dataclasses.dataclass
 class Params:
@@ -73,6 +77,7 @@ class Params:
     integrator: int = INTEG_IFRK4
     scalar_on: int = 1
     record_every: int = 10
+    nonlinear_form: int = NL_ROTATIONAL
 
     @property
     def D(self) -> float:
@@ -262,7 +267,7 @@ def rhs_nonlinear(uh, ph, g: Grid, p: Params):
     du/dt  = P(u x omega)_hat + A u_hat 1[0<|k|^2<=kF^2]
     dphi/dt = -(u.grad phi)_hat - beta u2_hat            (Eq. 8)"""
     A = forcing_amplitude(uh, g, p)
-    nl = nonlinear_rotational(uh, g)
+    nl = nonlinear_convective(uh, g) if p.nonlinear_form == NL_CONVECTIVE else nonlinear_rotational(uh, g)
     b = band(g, p.kF)
     ru = [nl[c] + np.where(b, A * uh[c], 0.0) for c in range(3)]
     if p.scalar_on:

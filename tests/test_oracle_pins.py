@@ -166,6 +166,17 @@ def test_pressure_balances_the_projection():
     assert max(np.abs(a - b).max() for a, b in zip(rebuilt, conv)) < 1e-12 * scale
 
 
+def test_convective_and_rotational_runs_agree():
+    # the two forms differ by a gradient that the projection removes, so whole
+    # forced runs with scalar agree to round-off
+    p = O.Params(N=24, nu=0.02, dt=0.005, ic=O.IC_TAYLOR_GREEN_NOISE, seed=3)
+    c = O.Params(**{**p.__dict__, "nonlinear_form": O.NL_CONVECTIVE})
+    u1, p1, _, _, _ = O.run(p, 10, with_records=False)
+    u2, p2, _, _, _ = O.run(c, 10, with_records=False)
+    assert np.abs(u1 - u2).max() < 1e-12 * np.abs(u1).max()
+    assert np.abs(p1 - p2).max() < 1e-12 * np.abs(p1).max()
+
+
 def test_nonlinear_terms_conserve_energy_and_variance():
     # sum_k Re(u* . N(u)) = 0 and sum_k Re(phi* . (u.grad phi)) = 0 on the
     # Galerkin-truncated system (3K < N makes the grid sums exact).
