@@ -58,6 +58,12 @@ typedef enum { PSC_IC_SPECTRUM_K4 = 0, PSC_IC_TAYLOR_GREEN_NOISE = 1, PSC_IC_PAP
  * psc_set_state (eps_inj unused); records report the equivalent rate
  * A = ln(factor) / dt. */
 typedef enum { PSC_FORCE_NONE = 0, PSC_FORCE_CONST_POWER = 1, PSC_FORCE_HOLD_ENERGY = 2 } psc_forcing;
+
+/* Form of the nonlinear term (section 2.3).  ROTATIONAL: P(u x omega), 9
+ * physical fields per right-hand side.  CONVECTIVE: -P((u.grad)u) as the paper
+ * writes it, with u and the 9 velocity gradients formed in physical space (12
+ * fields; a larger workspace).  The two agree to round-off on the retained set. */
+typedef enum { PSC_NL_ROTATIONAL = 0, PSC_NL_CONVECTIVE = 1 } psc_nonlinear;
 typedef enum { PSC_INTEG_IFRK4 = 0, PSC_INTEG_RK4 = 1 } psc_integrator;
 
 /* Problem statement (Table 2 of the paper; Sc and beta from section 2.3).
@@ -81,7 +87,7 @@ typedef struct {
   double ic_energy;     /* target K of the random IC (u_rms = 1 gives 1.5)            */
   double ic_noise_frac; /* Taylor-Green IC: noise energy as a fraction of 1/8         */
   int32_t scalar_on;    /* 0: phi is held at zero                                     */
-  int32_t reserved;
+  int32_t nonlinear_form; /* psc_nonlinear                                            */
 } psc_params;
 
 /* One statistics record of the current state (section 2.3): Table 1,

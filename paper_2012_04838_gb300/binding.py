@@ -26,7 +26,7 @@ class CParams(ct.Structure):
         ("kF", ct.c_double), ("eps_inj", ct.c_double), ("dt", ct.c_double), ("cfl", ct.c_double),
         ("seed", ct.c_uint64), ("ic", ct.c_int32), ("record_every", ct.c_int32),
         ("ic_energy", ct.c_double), ("ic_noise_frac", ct.c_double),
-        ("scalar_on", ct.c_int32), ("reserved", ct.c_int32),
+        ("scalar_on", ct.c_int32), ("nonlinear_form", ct.c_int32),
     ]
 
 
@@ -51,6 +51,7 @@ PSC_OK, PSC_EINVAL, PSC_ENOMEM_BUDGET, PSC_ECUDA, PSC_EUNSTABLE, PSC_ETIMEOUT, P
 FP64, FP32_MIXED = 0, 1
 IC_SPECTRUM_K4, IC_TAYLOR_GREEN_NOISE, IC_PAPER_EQ9 = 0, 1, 2
 FORCE_NONE, FORCE_CONST_POWER, FORCE_HOLD_ENERGY = 0, 1, 2
+NL_ROTATIONAL, NL_CONVECTIVE = 0, 1
 INTEG_IFRK4, INTEG_RK4 = 0, 1
 
 # every entry point of include/psc.h: (name, restype, argtypes)
@@ -145,9 +146,10 @@ class Params:
     ic_energy: float = 1.5
     ic_noise_frac: float = 0.01
     scalar_on: int = 1
+    nonlinear_form: int = 0  # NL_ROTATIONAL
 
     def c(self) -> CParams:
-        return CParams(**{f.name: getattr(self, f.name) for f in dataclasses.fields(self)}, reserved=0)
+        return CParams(**{f.name: getattr(self, f.name) for f in dataclasses.fields(self)})
 
 
 def workspace_size(p: Params) -> int:

@@ -92,13 +92,13 @@ struct Layout {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static Layout make_layout(const Dims& d, int fp64, int xwarps) {
+static Layout make_layout(const Dims& d, int fp64, int xwarps, int convective) {
   const size_t cs = fp64 ? 16 : 8, rs = fp64 ? 8 : 4;
   const size_t S = (size_t)d.S, zs = (size_t)d.zs, ys = (size_t)d.ys;
   size_t zreg = Z_NSTREAM * zs;
   if (4 * ys > zreg) zreg = 4 * ys;
   if (4 * S > zreg) zreg = 4 * S;
-  size_t yreg = Y_NSTREAM * ys * cs;
+  size_t yreg = (size_t)(convective ? Y_NSTREAM : Y_NSTREAM_ROT) * ys * cs;
   if (4 * zs * cs > yreg) yreg = 4 * zs * cs;
   if (3 * S * 16 > yreg) yreg = 3 * S * 16;  // FP64 scratch of the initial condition
   const int nsh = num_shells(d.N);
@@ -200,6 +200,8 @@ static psc_status check_params(const psc_params* p) {
   if (p->record_every < 1) return fail(PSC_EINVAL, "record_every must be >= 1");
   if (p->forcing != PSC_FORCE_NONE && p->forcing != PSC_FORCE_CONST_POWER && p->forcing != PSC_FORCE_HOLD_ENERGY)
     return fail(PSC_EINVAL, "bad forcing");
+  if (p->nonlinear_form != PSC_NL_ROTATIONAL && p->nonlinear_form != PSC_NL_CONVECTIVE)
+    return fail(PSC_EINVAL, "bad nonlinear_form");
   if (p->integrator != PSC_INTEG_IFRK4 && p->integrator != PSC_INTEG_RK4) return fail(PSC_EINVAL, "bad integrator");
   if (p->ic < 0 || p->ic > 2) return fail(PSC_EINVAL, "bad ic");
   if (!(p->kF >= 0.0) || !(p->eps_inj >= 0.0)) return fail(PSC_EINVAL, "kF and eps_inj must be >= 0");
@@ -231,7 +233,8 @@ psc_status psc_workspace_size(const psc_params* p, size_t* bytes) {
   if (s != PSC_OK) return s;
   if (!bytes) return fail(PSC_EINVAL, "null bytes");
   const PassTable* tb = pick_table(p);
-  *bytes = make_layout(make_dims(p->N), p->precision == PSC_FP64, tb->xwarps).total;
+  *bytes = make_layout(make_dims(p->N), p->precision == PSC_FP64, tb->xwarps,
+                       p->nonlinear_form == PSC_NL_CONVECTIVE).total;
   return PSC_OK;
 }
 
@@ -241,7 +244,8 @@ psc_status psc_create(const psc_params* p, void* dev_ws, size_t ws_bytes, void* 
   if (!out || !dev_ws) return fail(PSC_EINVAL, "null workspace or output handle");
   if (((uintptr_t)dev_ws & 255) != 0) return fail(PSC_EINVAL, "workspace must be 256-byte aligned");
   const PassTable* tb = pick_table(p);
-  Layout L = make_layout(make_dims(p->N), p->precision == PSC_FP64, tb->xwarps);
+  Layout L = make_layout(make_dims(p->N), p->precision == PSC_FP64, tb->xwarps,
+                         p->nonlinear_form == PSC_NL_CONVECTIVE);
   if (ws_bytes < L.total)
     return fail(PSC_ENOMEM_BUDGET, "workspace of " + std::to_string(ws_bytes) + " bytes < required " +
                                        std::to_string(L.total));
@@ -441,9 +445,12 @@ void rhs_passes(psc_sim* s, const void* in, bool umax, bool step_start = false) 
   a.want_umax = umax ? 1 : 0;
   if (umax) cudaMemsetAsync(&s->ctrl->umax_bits, 0, sizeof(unsigned long long), s->st);
   launch_famp<T>(s, in, step_start);
-  launch(s, PSC_K_ZINV, 1, [&] { s->tb->zinv(a, false, s->wv[SP_ZINV]); });
-  launch(s, PSC_K_YINV, 1, [&] { s->tb->yinv(a, false, s->wv[SP_YINV]); });
-  launch(s, PSC_K_XPASS, 1, [&] { s->tb->xpass(a, XMODE_RHS); });
+  // the convective form takes the 8 z-stage streams of the statistics pass and
+  // d_y u_z, d_z u_y separately at the y stage
+  const bool conv = s->p.nonlinear_form == PSC_NL_CONVECTIVE;
+  launch(s, PSC_K_ZINV, 1, [&] { s->tb->zinv(a, conv, s->wv[SP_ZINV]); });
+  launch(s, PSC_K_YINV, 1, [&] { s->tb->yinv(a, conv ? YMODE_CONVECTIVE : YMODE_RHS, s->wv[SP_YINV]); });
+  launch(s, PSC_K_XPASS, 1, [&] { s->tb->xpass(a, conv ? XMODE_CONVECTIVE : XMODE_RHS); });
   if (umax && s->p.cfl > 0.0) {
     launch(s, PSC_K_OTHER, 1, [&] {
       k_cfl<<<1, 32, 0, s->st>>>(s->ctrl, s->p.cfl, 2.0 * M_PI / s->p.N, s->p.record_every);
@@ -493,7 +500,7 @@ psc_status do_pressure(psc_sim* s, void* out) {
   const void* U = s->ws + s->L.U;
   PassArgs a = pass_args(s, U);
   launch(s, PSC_K_ZINV, 1, [&] { s->tb->zinv(a, false, s->wv[SP_ZINV]); });
-  launch(s, PSC_K_YINV, 1, [&] { s->tb->yinv(a, false, s->wv[SP_YINV]); });
+  launch(s, PSC_K_YINV, 1, [&] { s->tb->yinv(a, YMODE_RHS, s->wv[SP_YINV]); });
   launch(s, PSC_K_XPASS, 1, [&] { s->tb->xpass(a, XMODE_PRESSURE); });
   launch(s, PSC_K_YFWD, 1, [&] { s->tb->yfwd(a, s->wv[SP_YFWD]); });
   launch(s, PSC_K_ZFWD, 1, [&] { s->tb->zfwd(a, s->wv[SP_ZFWD]); });
@@ -541,7 +548,7 @@ psc_status do_stats(psc_sim* s, double* Ek, double* Ephi, int cap, int* nshell, 
   launch_famp<T>(s, U);
   launch(s, PSC_K_OTHER, 3, [&] {
     s->tb->zinv(a, true, s->wv[SP_ZINV]);
-    s->tb->yinv(a, true, s->wv[SP_YINV]);
+    s->tb->yinv(a, YMODE_STATS, s->wv[SP_YINV]);
     s->tb->xpass(a, XMODE_STATS);
   });
   double* shells = (double*)(s->ws + s->L.shells);
@@ -677,7 +684,7 @@ psc_status autotune(psc_sim* s) {
   auto run = [&](int p, int v) {
     switch (p) {
       case SP_ZINV: s->tb->zinv(a, false, v); break;
-      case SP_YINV: s->tb->yinv(a, false, v); break;
+      case SP_YINV: s->tb->yinv(a, YMODE_RHS, v); break;
       case SP_YFWD: s->tb->yfwd(a, v); break;
       default: s->tb->zfwd(a, v); break;
     }

@@ -53,7 +53,9 @@ struct Ctrl {
 
 // Streams of the intermediate buffers (indices into zb / yb).
 enum { Z_UX, Z_UY, Z_UZ, Z_DZUY, Z_DZUX, Z_PHI, Z_DZPHI, Z_DZUZ, Z_NSTREAM };
-enum { Y_UX, Y_UY, Y_UZ, Y_WX, Y_DZUX, Y_DYUX, Y_PHI, Y_DYPHI, Y_DZPHI, Y_DYUY, Y_DZUZ, Y_NSTREAM };
+// (with the convective form the Y_WX stream holds d_y u_z, and Y_DZUY is added)
+enum { Y_UX, Y_UY, Y_UZ, Y_WX, Y_DZUX, Y_DYUX, Y_PHI, Y_DYPHI, Y_DZPHI, Y_DYUY, Y_DZUZ, Y_DZUY, Y_NSTREAM };
+constexpr int Y_NSTREAM_ROT = Y_DZUY;  // streams the rotational form and the statistics use
 
 struct PassArgs {
   Dims d;
@@ -72,14 +74,17 @@ struct PassArgs {
 
 // X-pass modes: the right-hand side (u x omega, u . grad phi); the statistics
 // moments; the pressure inputs (u x omega and |u|^2/2 in place of the scalar term)
-enum { XMODE_RHS = 0, XMODE_STATS = 1, XMODE_PRESSURE = 2 };
+enum { XMODE_RHS = 0, XMODE_STATS = 1, XMODE_PRESSURE = 2, XMODE_CONVECTIVE = 3 };
+// y-inverse stream sets: the right-hand side (9), the statistics (11), the
+// convective form (12)
+enum { YMODE_RHS = 0, YMODE_STATS = 1, YMODE_CONVECTIVE = 2 };
 
 // Strided passes come in tile-width variants v (index into widths[]).
 enum { SP_ZINV = 0, SP_YINV = 1, SP_YFWD = 2, SP_ZFWD = 3, SP_N = 4 };
 
 struct PassTable {
   void (*zinv)(const PassArgs&, bool stats, int v);
-  void (*yinv)(const PassArgs&, bool stats, int v);
+  void (*yinv)(const PassArgs&, int ymode, int v);
   void (*xpass)(const PassArgs&, int mode);
   void (*yfwd)(const PassArgs&, int v);
   void (*zfwd)(const PassArgs&, int v);

@@ -214,7 +214,7 @@ k_zinv(PassArgs a) {
   }
 }
 
-template <typename T, int N, bool STATS, int W>
+template <typename T, int N, int YM, int W>
 __global__ void __launch_bounds__(StridedCfg<T, N, W>::THREADS, StridedCfg<T, N, W>::MINB)
 k_yinv(PassArgs a) {
   using C = typename CT<T>::type;
@@ -231,7 +231,7 @@ k_yinv(PassArgs a) {
   const long long zs = (long long)N * P * M, ys = (long long)N * N * M;
   const C zero = mk(T(0), T(0));
   // (kind, s1, s2, out): kind 0 = s1, 1 = i ky s1, 2 = i ky s1 - s2
-  constexpr int nt = STATS ? 11 : 9;
+  constexpr int nt = YM == YMODE_CONVECTIVE ? 12 : YM == YMODE_STATS ? 11 : 9;
 #pragma unroll 1
   for (int tr = 0; tr < nt; ++tr) {
     int kind, s1, s2 = 0, so;
@@ -239,14 +239,16 @@ k_yinv(PassArgs a) {
       case 0: kind = 0; s1 = Z_UX; so = Y_UX; break;
       case 1: kind = 0; s1 = Z_UY; so = Y_UY; break;
       case 2: kind = 0; s1 = Z_UZ; so = Y_UZ; break;
-      case 3: kind = 2; s1 = Z_UZ; s2 = Z_DZUY; so = Y_WX; break;  // omega_x = d_y u_z - d_z u_y
+      case 3:  // omega_x = d_y u_z - d_z u_y (convective form: d_y u_z alone)
+        kind = YM == YMODE_CONVECTIVE ? 1 : 2; s1 = Z_UZ; s2 = Z_DZUY; so = Y_WX; break;
       case 4: kind = 0; s1 = Z_DZUX; so = Y_DZUX; break;
       case 5: kind = 1; s1 = Z_UX; so = Y_DYUX; break;
       case 6: kind = 0; s1 = Z_PHI; so = Y_PHI; break;
       case 7: kind = 1; s1 = Z_PHI; so = Y_DYPHI; break;
       case 8: kind = 0; s1 = Z_DZPHI; so = Y_DZPHI; break;
       case 9: kind = 1; s1 = Z_UY; so = Y_DYUY; break;
-      default: kind = 0; s1 = Z_DZUZ; so = Y_DZUZ; break;
+      case 10: kind = 0; s1 = Z_DZUZ; so = Y_DZUZ; break;
+      default: kind = 0; s1 = Z_DZUY; so = Y_DZUY; break;
     }
     const long long rowz = (long long)z * P * M + ix;
     strided_fft<T, N, W, +1>(
@@ -637,6 +639,96 @@ k_xpass(PassArgs a) {
                    }
                  },
                  ex, tw, t);
+    } else if constexpr (MODE == XMODE_CONVECTIVE) {
+      // -(u.grad)u and u.grad phi from u, its nine gradients and grad phi; with
+      // this stream set Y_WX holds d_y u_z and Y_DZUY holds d_z u_y
+      T ux[J2][R2], uy[J2][R2], uz[J2][R2], aa[J2][R2], bb[J2][R2];
+      auto getu = [&](int c, int j, int k2) -> T {
+        if constexpr (XC::STASH) return stash[c * N + pos(j, k2)];
+        else return c == 0 ? ux[j][k2] : (c == 1 ? uy[j][k2] : uz[j][k2]);
+      };
+      auto putu = [&](int c, int j, int k2, T v) {
+        if constexpr (XC::STASH) {
+          stash[c * N + pos(j, k2)] = v;
+        } else {
+          if (c == 0) ux[j][k2] = v;
+          else if (c == 1) uy[j][k2] = v;
+          else uz[j][k2] = v;
+        }
+      };
+      auto store = [&](int s0) {
+        return [&, s0](int kx, C X1, C X2) {
+          if (!valid) return;
+          const long long i0 = line * M + kx;
+          if (PSC_OK_INDEX(i0 + (s0 + 1) * ys, 4 * ys, a.ctrl)) {
+            xb[s0 * ys + i0] = X1;
+            xb[(s0 + 1) * ys + i0] = X2;
+          }
+        };
+      };
+      // (u1, u2)
+      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UY, kx); }, z, ex, tw, t, scale);
+#pragma unroll
+      for (int j = 0; j < J2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) { putu(0, j, k2, z[j][k2].x); putu(1, j, k2, z[j][k2].y); }
+      // (u3, d1 u1)
+      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UZ, kx); x2 = mul_ik(Y(Y_UX, kx), T(kx)); }, z, ex, tw, t,
+                 scale);
+#pragma unroll
+      for (int j = 0; j < J2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) {
+          putu(2, j, k2, z[j][k2].x);
+          aa[j][k2] = getu(0, j, k2) * z[j][k2].y;
+          if (a.want_umax) um = max_keep_nan(um, fabs(getu(0, j, k2)) + fabs(getu(1, j, k2)) + fabs(z[j][k2].x));
+        }
+      // (d2 u1, d3 u1): aa = (u.grad) u1
+      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DYUX, kx); x2 = Y(Y_DZUX, kx); }, z, ex, tw, t, scale);
+#pragma unroll
+      for (int j = 0; j < J2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) aa[j][k2] += getu(1, j, k2) * z[j][k2].x + getu(2, j, k2) * z[j][k2].y;
+      // (d1 u2, d2 u2)
+      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_UY, kx), T(kx)); x2 = Y(Y_DYUY, kx); }, z, ex, tw, t,
+                 scale);
+#pragma unroll
+      for (int j = 0; j < J2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) bb[j][k2] = getu(0, j, k2) * z[j][k2].x + getu(1, j, k2) * z[j][k2].y;
+      // (d3 u2, d1 u3): bb = (u.grad) u2; aa starts (u.grad) u3
+      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZUY, kx); x2 = mul_ik(Y(Y_UZ, kx), T(kx)); }, z, ex, tw, t,
+                 scale);
+#pragma unroll
+      for (int j = 0; j < J2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) {
+          const T b2 = bb[j][k2] + getu(2, j, k2) * z[j][k2].x, c3 = getu(0, j, k2) * z[j][k2].y;
+          z[j][k2] = mk(-aa[j][k2], -b2);  // (NL1, NL2)
+          aa[j][k2] = c3;
+        }
+      xfwd<T, N>(z, store(0), ex, tw, t);
+      // (d2 u3, d3 u3): aa = (u.grad) u3
+      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_WX, kx); x2 = Y(Y_DZUZ, kx); }, z, ex, tw, t, scale);
+#pragma unroll
+      for (int j = 0; j < J2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) aa[j][k2] += getu(1, j, k2) * z[j][k2].x + getu(2, j, k2) * z[j][k2].y;
+      // (dphi/dx1, dphi/dx2)
+      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_PHI, kx), T(kx)); x2 = Y(Y_DYPHI, kx); }, z, ex, tw, t,
+                 scale);
+#pragma unroll
+      for (int j = 0; j < J2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) bb[j][k2] = getu(0, j, k2) * z[j][k2].x + getu(1, j, k2) * z[j][k2].y;
+      // (dphi/dx3, 0)
+      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZPHI, kx); x2 = zero; }, z, ex, tw, t, scale);
+#pragma unroll
+      for (int j = 0; j < J2; ++j)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2)
+          z[j][k2] = mk(-aa[j][k2], bb[j][k2] + getu(2, j, k2) * z[j][k2].x);  // (NL3, u.grad phi)
+      xfwd<T, N>(z, store(2), ex, tw, t);
     } else {
       // statistics: moments of the diagonal velocity gradients and the scalar
       // gradient (Eqs. 11-12), |omega|^2, u.u, phi u2, phi^2 (Eq. 13)
@@ -795,11 +887,16 @@ template <typename T, int N> struct Passes {
     if (stats) { prep(k_zinv<T, N, true, W>, sm); k_zinv<T, N, true, W><<<grid, block, sm, a.st>>>(a); }
     else { prep(k_zinv<T, N, false, W>, sm); k_zinv<T, N, false, W><<<grid, block, sm, a.st>>>(a); }
   }
-  template <int W> static void yinv_w(const PassArgs& a, bool stats) {
+  template <int W, int YM> static void yinv_m(const PassArgs& a) {
     constexpr size_t sm = StridedSmem<T, N, W>::BYTES;
     dim3 grid((M + W - 1) / W, N), block(W, TPL);
-    if (stats) { prep(k_yinv<T, N, true, W>, sm); k_yinv<T, N, true, W><<<grid, block, sm, a.st>>>(a); }
-    else { prep(k_yinv<T, N, false, W>, sm); k_yinv<T, N, false, W><<<grid, block, sm, a.st>>>(a); }
+    prep(k_yinv<T, N, YM, W>, sm);
+    k_yinv<T, N, YM, W><<<grid, block, sm, a.st>>>(a);
+  }
+  template <int W> static void yinv_w(const PassArgs& a, int ym) {
+    if (ym == YMODE_STATS) yinv_m<W, YMODE_STATS>(a);
+    else if (ym == YMODE_CONVECTIVE) yinv_m<W, YMODE_CONVECTIVE>(a);
+    else yinv_m<W, YMODE_RHS>(a);
   }
   template <int W> static void yfwd_w(const PassArgs& a) {
     constexpr size_t sm = StridedSmem<T, N, W>::BYTES;
@@ -823,7 +920,7 @@ template <typename T, int N> struct Passes {
   static constexpr int NV = STAGED16 ? 5 : STAGED ? 4 : (WV0 != WV1 ? 2 : 1);
   static constexpr unsigned MASK_INV = (1u << NV) - 1u;
   static constexpr unsigned MASK_FWD = STAGED16 ? 0xFu : (1u << NV) - 1u;
-  template <int W, int PASS, bool STATS> static bool launch_s(const PassArgs& a) {
+  template <int W, int PASS, int MODE> static bool launch_s(const PassArgs& a) {
     if constexpr (STAGED) {
       using TL = StagedTile<T, N, W, PASS == SP_ZINV || PASS == SP_YINV>;
       CUtensorMap m;
@@ -843,41 +940,49 @@ template <typename T, int N> struct Passes {
         rows = P;
       }
       if (!ok) return false;
-      prep(k_strided_s<T, N, W, PASS, STATS>, TL::SMEM);
-      k_strided_s<T, N, W, PASS, STATS><<<dim3((M + W - 1) / W, rows), dim3(W, TPL), TL::SMEM, a.st>>>(a, m);
+      prep(k_strided_s<T, N, W, PASS, MODE>, TL::SMEM);
+      k_strided_s<T, N, W, PASS, MODE><<<dim3((M + W - 1) / W, rows), dim3(W, TPL), TL::SMEM, a.st>>>(a, m);
       return true;
     } else {
       (void)a;
       return false;
     }
   }
-  template <int PASS> static bool staged(const PassArgs& a, bool stats, int v) {
-    if constexpr (PASS == SP_ZINV || PASS == SP_YINV) {
-      if (v == 2) return stats ? launch_s<4, PASS, true>(a) : launch_s<4, PASS, false>(a);
-      if constexpr (STAGED16) {
-        if (v == 4) return stats ? launch_s<16, PASS, true>(a) : launch_s<16, PASS, false>(a);
-      }
-      return stats ? launch_s<8, PASS, true>(a) : launch_s<8, PASS, false>(a);
+  template <int PASS, int W> static bool staged_w(const PassArgs& a, int mode) {
+    if constexpr (PASS == SP_YINV) {
+      if (mode == YMODE_STATS) return launch_s<W, PASS, YMODE_STATS>(a);
+      if (mode == YMODE_CONVECTIVE) return launch_s<W, PASS, YMODE_CONVECTIVE>(a);
+      return launch_s<W, PASS, YMODE_RHS>(a);
+    } else if constexpr (PASS == SP_ZINV) {
+      return mode ? launch_s<W, PASS, 1>(a) : launch_s<W, PASS, 0>(a);
     } else {
-      (void)stats;
-      return v == 2 ? launch_s<4, PASS, false>(a) : launch_s<8, PASS, false>(a);
+      (void)mode;
+      return launch_s<W, PASS, 0>(a);
     }
+  }
+  // mode: z-inverse 0/1 (right-hand side / 8 streams), y-inverse YMODE_*
+  template <int PASS> static bool staged(const PassArgs& a, int mode, int v) {
+    if (v == 2) return staged_w<PASS, 4>(a, mode);
+    if constexpr (STAGED16 && (PASS == SP_ZINV || PASS == SP_YINV)) {
+      if (v == 4) return staged_w<PASS, 16>(a, mode);
+    }
+    return staged_w<PASS, 8>(a, mode);
   }
   // a staged variant falls back to variant 0 if its tensor map cannot be made
   static void zinv(const PassArgs& a, bool stats, int v) {
-    if (v >= 2 && staged<SP_ZINV>(a, stats, v)) return;
+    if (v >= 2 && staged<SP_ZINV>(a, stats ? 1 : 0, v)) return;
     v == 1 ? zinv_w<WV1>(a, stats) : zinv_w<WV0>(a, stats);
   }
-  static void yinv(const PassArgs& a, bool stats, int v) {
-    if (v >= 2 && staged<SP_YINV>(a, stats, v)) return;
-    v == 1 ? yinv_w<WV1>(a, stats) : yinv_w<WV0>(a, stats);
+  static void yinv(const PassArgs& a, int ym, int v) {
+    if (v >= 2 && staged<SP_YINV>(a, ym, v)) return;
+    v == 1 ? yinv_w<WV1>(a, ym) : yinv_w<WV0>(a, ym);
   }
   static void yfwd(const PassArgs& a, int v) {
-    if (v >= 2 && staged<SP_YFWD>(a, false, v)) return;
+    if (v >= 2 && staged<SP_YFWD>(a, 0, v)) return;
     v == 1 ? yfwd_w<WV1>(a) : yfwd_w<WV0>(a);
   }
   static void zfwd(const PassArgs& a, int v) {
-    if (v >= 2 && staged<SP_ZFWD>(a, false, v)) return;
+    if (v >= 2 && staged<SP_ZFWD>(a, 0, v)) return;
     v == 1 ? zfwd_w<WV1>(a) : zfwd_w<WV0>(a);
   }
   // the right-hand side at N = 1024 (FP32) stages its rows through shared memory
@@ -897,19 +1002,20 @@ template <typename T, int N> struct Passes {
     }
     return n[dev];
   }
-  static void xpass(const PassArgs& a, int mode) {
-    if (mode == XMODE_PRESSURE) {
-      if constexpr (X2) {
-        const size_t sm2 = X2Cfg<T, N>::SMEM;
-        prep(k_xpass2<T, N, XMODE_PRESSURE>, sm2);
-        k_xpass2<T, N, XMODE_PRESSURE><<<xgrid(), 128, sm2, a.st>>>(a);
-      } else {
-        const size_t sm = XCfg<T, N>::SMEM;
-        prep(k_xpass<T, N, XMODE_PRESSURE>, sm);
-        k_xpass<T, N, XMODE_PRESSURE><<<xgrid(), dim3(32 * XCfg<T, N>::WARPS), sm, a.st>>>(a);
-      }
-      return;
+  template <int MODE> static void xpass_plain(const PassArgs& a) {
+    if constexpr (X2) {
+      const size_t sm2 = X2Cfg<T, N>::SMEM;
+      prep(k_xpass2<T, N, MODE>, sm2);
+      k_xpass2<T, N, MODE><<<xgrid(), 128, sm2, a.st>>>(a);
+    } else {
+      const size_t sm = XCfg<T, N>::SMEM;
+      prep(k_xpass<T, N, MODE>, sm);
+      k_xpass<T, N, MODE><<<xgrid(), dim3(32 * XCfg<T, N>::WARPS), sm, a.st>>>(a);
     }
+  }
+  static void xpass(const PassArgs& a, int mode) {
+    if (mode == XMODE_PRESSURE) return xpass_plain<XMODE_PRESSURE>(a);
+    if (mode == XMODE_CONVECTIVE) return xpass_plain<XMODE_CONVECTIVE>(a);
     if constexpr (X2S) {
       if (mode == XMODE_RHS) {
         using SC = X2SCfg<T, N>;

@@ -112,8 +112,12 @@ __device__ __forceinline__ void strided_fft_regs(typename CT<T>::type (&in)[Plan
 // Transform tr of a pass: source field / stream, how its line is formed, and
 // the output stream.  kind 0: the source; 1: i k times the source; 2: i k
 // times the source minus stream s2 (omega_x = d_y u_z - d_z u_y).
-template <int PASS, bool STATS> struct StagedPlan {
-  static constexpr int NT = PASS == SP_ZINV ? (STATS ? 8 : 7) : PASS == SP_YINV ? (STATS ? 11 : 9) : 4;
+// MODE: z-inverse 0 (7 streams) or 1 (8, for the statistics and the convective
+// form); y-inverse YMODE_RHS (9), YMODE_STATS (11) or YMODE_CONVECTIVE (12).
+template <int PASS, int MODE> struct StagedPlan {
+  static constexpr int NT = PASS == SP_ZINV   ? (MODE ? 8 : 7)
+                            : PASS == SP_YINV ? (MODE == YMODE_CONVECTIVE ? 12 : MODE == YMODE_STATS ? 11 : 9)
+                                              : 4;
   __device__ __forceinline__ static void get(int tr, int& src, int& kind, int& s2, int& out) {
     s2 = 0;
     if constexpr (PASS == SP_ZINV) {
@@ -132,14 +136,16 @@ template <int PASS, bool STATS> struct StagedPlan {
         case 0: src = Z_UX; kind = 0; out = Y_UX; break;
         case 1: src = Z_UY; kind = 0; out = Y_UY; break;
         case 2: src = Z_UZ; kind = 0; out = Y_UZ; break;
-        case 3: src = Z_UZ; kind = 2; s2 = Z_DZUY; out = Y_WX; break;
+        case 3:  // omega_x = d_y u_z - d_z u_y (convective form: d_y u_z alone)
+          src = Z_UZ; kind = MODE == YMODE_CONVECTIVE ? 1 : 2; s2 = Z_DZUY; out = Y_WX; break;
         case 4: src = Z_DZUX; kind = 0; out = Y_DZUX; break;
         case 5: src = Z_UX; kind = 1; out = Y_DYUX; break;
         case 6: src = Z_PHI; kind = 0; out = Y_PHI; break;
         case 7: src = Z_PHI; kind = 1; out = Y_DYPHI; break;
         case 8: src = Z_DZPHI; kind = 0; out = Y_DZPHI; break;
         case 9: src = Z_UY; kind = 1; out = Y_DYUY; break;
-        default: src = Z_DZUZ; kind = 0; out = Y_DZUZ; break;
+        case 10: src = Z_DZUZ; kind = 0; out = Y_DZUZ; break;
+        default: src = Z_DZUY; kind = 0; out = Y_DZUY; break;
       }
     } else {
       src = tr;
@@ -155,7 +161,7 @@ template <int PASS, bool STATS> struct StagedPlan {
 //   y-inverse: z-stage streams, 2D {2M, Z_NSTREAM N P}
 //   y-forward: x-pass output,   2D {2M, 4 N N}
 //   z-forward: y-forward output, 3D {2M, P (ky), 4N (stream, z)}
-template <typename T, int N, int W, int PASS, bool STATS>
+template <typename T, int N, int W, int PASS, int MODE>
 __global__ void __launch_bounds__(W * PlanD<N>::TPL,
                                   StagedTile<T, N, W, PASS == SP_ZINV || PASS == SP_YINV>::MINB)
 k_strided_s(PassArgs a, const __grid_constant__ CUtensorMap tm) {
@@ -163,7 +169,7 @@ k_strided_s(PassArgs a, const __grid_constant__ CUtensorMap tm) {
   using PL = PlanD<N>;
   constexpr bool INV = PASS == SP_ZINV || PASS == SP_YINV;
   using TL = StagedTile<T, N, W, INV>;
-  using SPL = StagedPlan<PASS, STATS>;
+  using SPL = StagedPlan<PASS, MODE>;
   constexpr int K = PL::K, M = PL::M, P = PL::P, R1 = PL::R1, R2 = PL::R2, TPL = PL::TPL, J1 = PL::J1;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);

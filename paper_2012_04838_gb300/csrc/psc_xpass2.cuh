@@ -313,6 +313,75 @@ __device__ __forceinline__ bool x2_rhs_row(const YF& Y, const HA& after_a, const
   return true;
 }
 
+// The convective form of one row: -(u.grad)u and u.grad phi from u, its nine
+// gradients and grad phi (8 inverse transforms of packed pairs, 2 forward).
+// With this stream set Y_WX holds d_y u_z and Y_DZUY holds d_z u_y.
+template <typename T, int N, class YF>
+__device__ __forceinline__ void x2_conv_row(const YF& Y, typename CT<T>::type* __restrict__ xb, long long line,
+                                            long long ys, typename CT<T>::type* ex,
+                                            const X2Roles<typename CT<T>::type>& q, T scale, bool want_umax, T& um,
+                                            Ctrl* ctrl) {
+  using C = typename CT<T>::type;
+  constexpr int M = X2Cfg<T, N>::K + 1;
+  const C zero = mk(T(0), T(0));
+  (void)ctrl;
+  C z[16];
+  const T s2 = scale * scale;  // the transforms are unscaled: each product carries 1/N^6
+  T u1[16], u2[16], u3[16], A[16], B[16];
+  auto out = [&](int s0) {
+    return [&, s0](int kx, C X1, C X2) {
+      const long long i0 = s0 * ys + line * M + kx;
+      if (PSC_OK_INDEX(i0 + ys, 4 * ys, ctrl)) { xb[i0] = X1; xb[i0 + ys] = X2; }
+    };
+  };
+  // (u1, u2)
+  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UY, kx); }, z, ex, q, scale);
+#pragma unroll
+  for (int b = 0; b < 16; ++b) { u1[b] = z[b].x; u2[b] = z[b].y; }
+  // (u3, d1 u1)
+  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UZ, kx); x2 = mul_ik(Y(Y_UX, kx), T(kx)); }, z, ex, q,
+                     scale);
+#pragma unroll
+  for (int b = 0; b < 16; ++b) {
+    u3[b] = z[b].x;
+    A[b] = u1[b] * z[b].y;
+    if (want_umax) um = max_keep_nan(um, fabs(u1[b]) + fabs(u2[b]) + fabs(u3[b]));
+  }
+  // (d2 u1, d3 u1): A = (u.grad) u1
+  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DYUX, kx); x2 = Y(Y_DZUX, kx); }, z, ex, q, scale);
+#pragma unroll
+  for (int b = 0; b < 16; ++b) A[b] += u2[b] * z[b].x + u3[b] * z[b].y;
+  // (d1 u2, d2 u2)
+  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_UY, kx), T(kx)); x2 = Y(Y_DYUY, kx); }, z, ex, q,
+                     scale);
+#pragma unroll
+  for (int b = 0; b < 16; ++b) B[b] = u1[b] * z[b].x + u2[b] * z[b].y;
+  // (d3 u2, d1 u3): B = (u.grad) u2; A starts (u.grad) u3
+  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZUY, kx); x2 = mul_ik(Y(Y_UZ, kx), T(kx)); }, z, ex, q,
+                     scale);
+#pragma unroll
+  for (int b = 0; b < 16; ++b) {
+    const T b2 = B[b] + u3[b] * z[b].x, c3 = u1[b] * z[b].y;
+    z[b] = mk(-A[b] * s2, -b2 * s2);  // (NL1, NL2)
+    A[b] = c3;
+  }
+  x2fwd<T, N>(z, out(0), ex, q);
+  // (d2 u3, d3 u3): A = (u.grad) u3
+  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_WX, kx); x2 = Y(Y_DZUZ, kx); }, z, ex, q, scale);
+#pragma unroll
+  for (int b = 0; b < 16; ++b) A[b] += u2[b] * z[b].x + u3[b] * z[b].y;
+  // (dphi/dx1, dphi/dx2)
+  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_PHI, kx), T(kx)); x2 = Y(Y_DYPHI, kx); }, z, ex,
+                     q, scale);
+#pragma unroll
+  for (int b = 0; b < 16; ++b) B[b] = u1[b] * z[b].x + u2[b] * z[b].y;
+  // (dphi/dx3, 0)
+  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZPHI, kx); x2 = zero; }, z, ex, q, scale);
+#pragma unroll
+  for (int b = 0; b < 16; ++b) z[b] = mk(-A[b] * s2, (B[b] + u3[b] * z[b].x) * s2);  // (NL3, u.grad phi)
+  x2fwd<T, N>(z, out(2), ex, q);
+}
+
 template <typename T>
 __device__ __forceinline__ double warp_sum_d(T v) {
   double d = (double)v;
@@ -365,6 +434,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : PSC_X2_MINB) k_xpass
       x2_rhs_row<T, N, MODE == XMODE_PRESSURE>(Y, [] {}, [] { return true; }, [] {}, xb, line, ys, ex, q, scale,
                        a.want_umax != 0,
                        um, a.ctrl);
+    } else if constexpr (MODE == XMODE_CONVECTIVE) {
+      x2_conv_row<T, N>(Y, xb, line, ys, ex, q, scale, a.want_umax != 0, um, a.ctrl);
     } else {
       // statistics (Eqs. 11-13): per pair, partial sums of the thread's 16
       // points, added in FP64 to the thread's accumulators (reduced over the

@@ -79,16 +79,35 @@ def test_fullsize_rhs_on_sparse_state_matches_triad_sums(sim):
     _sparse_check(sim, N, B.FP32_MIXED, 1)
 
 
+@pytest.mark.parametrize("form", [B.NL_ROTATIONAL, B.NL_CONVECTIVE], ids=["rotational", "convective"])
 @pytest.mark.parametrize("prec", [B.FP32_MIXED, B.FP64], ids=["fp32", "fp64"])
-def test_512_rhs_on_sparse_state_matches_triad_sums(prec):
+def test_512_rhs_on_sparse_state_matches_triad_sums(prec, form):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    p = B.Params(N=512, precision=prec, nu=8.419e-4, beta=1.0, eps_inj=0.1, kF=2.0)
+    p = B.Params(N=512, precision=prec, nu=8.419e-4, beta=1.0, eps_inj=0.1, kF=2.0, nonlinear_form=form)
     s = B.Simulation(p, device="cuda:0")
     try:
         _sparse_check(s, 512, prec, 2)
     finally:
         s.close()
+
+
+def test_fullsize_convective_rhs_on_sparse_state_matches_triad_sums():
+    """The convective form (u, nine gradients, 12 y-stage streams) at 1024^3:
+    after projection it equals the rotational triad sums."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p = B.Params(N=N, precision=B.FP32_MIXED, nu=3.341e-4, beta=1.0, eps_inj=0.1, kF=2.0,
+                 nonlinear_form=B.NL_CONVECTIVE)
+    free, _ = torch.cuda.mem_get_info()
+    if free < B.workspace_size(p) + 16e9:
+        pytest.skip("not enough device memory for the 1024^3 case")
+    s = B.Simulation(p, device="cuda:0")
+    try:
+        _sparse_check(s, N, B.FP32_MIXED, 4)
+    finally:
+        s.close()
+        torch.cuda.empty_cache()
 
 
 def test_fullsize_initial_condition_properties(sim):

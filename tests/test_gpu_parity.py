@@ -31,7 +31,8 @@ def oparams(p: "B.Params") -> O.Params:
     return O.Params(N=p.N, nu=p.nu, Sc=p.Sc, beta=p.beta, forcing=p.forcing, kF=p.kF,
                     eps_inj=p.eps_inj, dt=p.dt, cfl=p.cfl, seed=p.seed, ic=p.ic,
                     ic_energy=p.ic_energy, ic_noise_frac=p.ic_noise_frac,
-                    integrator=p.integrator, scalar_on=p.scalar_on, record_every=p.record_every)
+                    integrator=p.integrator, scalar_on=p.scalar_on, record_every=p.record_every,
+                    nonlinear_form=p.nonlinear_form)
 
 
 def oracle_rhs(x, p):
@@ -378,3 +379,40 @@ def test_pressure_of_taylor_green_at_full_size(dev, N):
     assert np.abs(got - ref).max() < 1e-6 * scale
     sim.close()
     torch.cuda.empty_cache()
+
+
+# ---------------------------------------------------------------- convective form
+
+@pytest.mark.parametrize("prec", PREC, ids=PNAME.get)
+@pytest.mark.parametrize("N", [16, 24, 48, 96, 192, 256])
+def test_convective_rhs_matches_oracle(dev, N, prec):
+    p = B.Params(N=N, precision=prec, nu=0.013, Sc=0.7, beta=1.1, eps_inj=0.1, kF=2.0,
+                 nonlinear_form=B.NL_CONVECTIVE)
+    sim = B.Simulation(p, device=dev)
+    x = as_input(random_compact_state(N, 700 + N, kpeak=4.0 if N < 128 else 8.0), prec)
+    got = sim.rhs(torch.from_numpy(x).to(dev)).cpu().numpy().astype(np.complex128)
+    ref = oracle_rhs(x, p)
+    assert rel(got, ref) < TOL_RHS[prec]
+    for f in range(4):
+        assert rel(got[f], ref[f]) < 10 * TOL_RHS[prec]
+    # and the rotational form on the same input agrees to the same tolerance
+    rot = B.Simulation(B.Params(**{**p.__dict__, "nonlinear_form": B.NL_ROTATIONAL}), device=dev)
+    other = rot.rhs(torch.from_numpy(x).to(dev)).cpu().numpy().astype(np.complex128)
+    assert rel(got, other) < 2 * TOL_RHS[prec]
+    sim.close()
+    rot.close()
+
+
+@pytest.mark.parametrize("prec", PREC, ids=PNAME.get)
+def test_convective_trajectory_matches_oracle(dev, prec):
+    N = 32
+    p = B.Params(N=N, precision=prec, nu=0.02, dt=0.005, ic=B.IC_TAYLOR_GREEN_NOISE, seed=1,
+                 nonlinear_form=B.NL_CONVECTIVE, cfl=0.5, record_every=5)
+    sim = B.Simulation(p, device=dev)
+    sim.init_field()
+    sim.step(20)
+    got = sim.get_state().cpu().numpy().astype(np.complex128)
+    uh, ph, _, _, _ = O.run(oparams(p), 20, with_records=False)
+    ref = full_to_compact(np.concatenate([uh, ph[None]]), N)
+    assert rel(got, ref) < TOL_TRAJ[prec]
+    sim.close()
