@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cufft", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--form", choices=["rotational", "convective"], default="rotational",
+                    help="nonlinear term of the timed workload (default: rotational u x omega)")
     ap.add_argument("--companion", action="store_true",
                     help="512^3 FP32-mixed and FP64 from the same IC, 200 steps, records compared "
                          "every 10 steps (error check of the 1024^3 FP32-mixed run)")
@@ -74,16 +76,19 @@ def whole_job_rate(steps_per_rank: int, world: int, ms_max: float) -> float:
     return world * steps_per_rank / (ms_max / 1000.0)
 
 
-def kernel_bytes(N: int, cbytes: int) -> dict:
+def kernel_bytes(N: int, cbytes: int, convective: bool = False) -> dict:
     """Algorithmic bytes per launch of each kernel kind (reads + writes of the
-    minimum data each pass must move; complex elements of `cbytes` bytes)."""
+    minimum data each pass must move; complex elements of `cbytes` bytes).
+    The convective form carries 8 z-stage and 12 y-stage streams instead of
+    7 and 9."""
     K = (N - 1) // 3
     M, P = K + 1, 2 * K + 1
     S, zs, ys = P * P * M, N * P * M, N * N * M
+    nz, ny = (8, 12) if convective else (7, 9)
     return {
-        "zinv": (4 * S + 7 * zs) * cbytes,
-        "yinv": (7 * zs + 9 * ys) * cbytes,
-        "xpass": (9 * ys + 4 * ys) * cbytes,
+        "zinv": (4 * S + nz * zs) * cbytes,
+        "yinv": (nz * zs + ny * ys) * cbytes,
+        "xpass": (ny * ys + 4 * ys) * cbytes,
         "yfwd": (4 * ys + 4 * zs) * cbytes,
         "zfwd": (4 * zs + 4 * S) * cbytes,
         # stage updates (complex values): 16 S at stage 1, 21 S at stages 2-3,
@@ -443,7 +448,8 @@ def main():
                      Sc=WORKLOAD["Sc"], beta=WORKLOAD["beta"], kF=WORKLOAD["kF"],
                      eps_inj=WORKLOAD["eps_inj"], cfl=WORKLOAD["cfl"], seed=WORKLOAD["seed"] + rank,
                      ic=psc.IC_SPECTRUM_K4, ic_energy=WORKLOAD["ic_energy"],
-                     record_every=WORKLOAD["record_every"])
+                     record_every=WORKLOAD["record_every"],
+                     nonlinear_form=psc.NL_CONVECTIVE if a.form == "convective" else psc.NL_ROTATIONAL)
     sim = psc.Simulation(prm, device=dev)
     stream = sim.stream
     sim.init_field()
@@ -479,7 +485,7 @@ def main():
     value = whole_job_rate(a.steps, world, ms)
 
     # roofline of the dominant kernel (per-launch device time from CUDA events)
-    kb = kernel_bytes(N, 8)
+    kb = kernel_bytes(N, 8, a.form == "convective")
     peak, peak_src = peaks()
     kinds = {k: v for k, v in prof.items() if k in kb and v[1] > 0}
     dom = max(kinds, key=lambda k: kinds[k][0])
@@ -508,7 +514,7 @@ def main():
            "config": {"workload": f"{N}^3 forced HIT + passive scalar, FP32-mixed "
                                   "(FP64 reductions and IF exponentials), CFL 0.5, records every 10 steps",
                       "N": N, "precision": "fp32_mixed", "nu": prm.nu, "Sc": prm.Sc, "kF": prm.kF,
-                      "eps_inj": prm.eps_inj, "record_every": rec_every,
+                      "eps_inj": prm.eps_inj, "record_every": rec_every, "nonlinear_form": a.form,
                       "l2": "inputs larger than L2 (state %.2f GB, working set %.1f GB)"
                             % (sim.state_bytes() / 1e9, psc.workspace_size(prm) / 1e9),
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
