@@ -205,13 +205,15 @@ def run_ensemble(dev):
     import paper_2012_04838_gb300 as psc
     from paper_2012_04838_gb300.serve import Server, make_params
     reqs = ensemble_requests()
-    res, summ = Server(budget_bytes=150e9, chunk=10 ** 9, device=dev).run(reqs)
+    res, summ = Server(budget_bytes=150e9, chunk=10 ** 9, device=dev, records="final").run(reqs)
     out = {"metric": "ensemble sims/hr", "value": summ["sims_per_hour"], "unit": "sims/hr",
            "boxes": len(reqs), "total_steps": sum(r.steps for r in reqs), "wall_s": summ["wall_s"],
            "grid_point_stages_per_s": summ["grid_point_stages_per_s"],
-           "graph_builds": summ["graph_builds"], "precision": "fp32_mixed",
+           "graph_builds": summ["graph_builds"], "graph_build_s": round(summ["graph_build_s"], 3),
+           "records": summ["records"], "precision": "fp32_mixed",
            "config": "64x64^3 + 16x96^3 + 4x128^3, k_max eta in [1,2], Sc in {0.7,1,2}, "
-                     "200-1000 steps, CFL 0.5, one graph replay per ensemble step"}
+                     "200-1000 steps, CFL 0.5, one graph replay per ensemble step, a statistics "
+                     "record of each box when it ends"}
     # plain FP64 single-run path on the same GPU: each box alone, no batching;
     # per-step time of one box per size x every box's step count
     per_step = {}

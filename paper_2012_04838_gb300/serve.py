@@ -80,10 +80,15 @@ class Server:
     """Admit, batch, step and retire runs on one device.
 
     budget_bytes: HBM the runs' workspaces may occupy together.
-    chunk: steps between scheduling decisions (and statistics records)."""
+    chunk: steps between scheduling decisions (and statistics records).
+    records: "chunk" takes a record of every active run after every chunk (the
+    stream of records a server returns); "final" only of each run when it ends."""
 
     def __init__(self, budget_bytes: float = 150e9, chunk: int = 50, device="cuda:0",
-                 clock=time.perf_counter, sleep=time.sleep):
+                 clock=time.perf_counter, sleep=time.sleep, records: str = "chunk"):
+        if records not in ("chunk", "final"):
+            raise ValueError("records must be 'chunk' or 'final'")
+        self.records = records
         import torch
         self.torch = torch
         self.budget = budget_bytes
@@ -102,7 +107,8 @@ class Server:
         batch = None
         dirty = True
         t0 = self.clock()
-        stats = dict(graph_builds=0, chunks=0, grid_point_stages=0.0, peak_active=0, peak_bytes=0)
+        stats = dict(graph_builds=0, graph_build_s=0.0, chunks=0, grid_point_stages=0.0, peak_active=0,
+                     peak_bytes=0, records=0)
         while pending or active:
             now = self.clock() - t0
             # admission: arrival order, while the next run's workspace fits the budget
@@ -126,10 +132,12 @@ class Server:
                 self.sleep(max(0.0, min(0.05, pending[0].arrival - now)))
                 continue
             if dirty:
+                tb = self.clock()
                 if batch is not None:
                     batch.close()
                 batch = B.Batch([a["sim"] for a in active], stream=self.stream)
                 stats["graph_builds"] += 1
+                stats["graph_build_s"] += self.clock() - tb
                 dirty = False
             n = min(self.chunk, min(a["left"] for a in active))
             batch.step(n)
@@ -139,11 +147,13 @@ class Server:
             for a in active:
                 a["left"] -= n
                 stats["grid_point_stages"] += 4.0 * n * a["req"].N ** 3
-                rec, E, Ep = a["sim"].stats()
-                rec["E"], rec["Ephi"] = E, Ep
-                a["records"].append(rec)
-                if on_record is not None:
-                    on_record(a["req"].rid, rec)
+                if self.records == "chunk" or a["left"] == 0:
+                    rec, E, Ep = a["sim"].stats()
+                    rec["E"], rec["Ephi"] = E, Ep
+                    a["records"].append(rec)
+                    stats["records"] += 1
+                    if on_record is not None:
+                        on_record(a["req"].rid, rec)
                 if a["left"] == 0:
                     finished.append(a)
             if finished:
@@ -159,7 +169,8 @@ class Server:
                     a["sim"].close()
                     del a["sim"]
                 dirty = True
-                torch.cuda.empty_cache()
+                if pending:  # hand freed memory back for the next admissions
+                    torch.cuda.empty_cache()
         if batch is not None:
             batch.close()
         wall = self.clock() - t0
