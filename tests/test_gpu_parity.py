@@ -358,8 +358,9 @@ def _embed(small, n1, n2):
     return big
 
 
-@pytest.mark.parametrize("N", [512, 1024])
-def test_pressure_of_taylor_green_at_full_size(dev, N):
+@pytest.mark.parametrize("N,prec", [(512, B.FP32_MIXED), (512, B.FP64), (1024, B.FP32_MIXED)],
+                         ids=["512-fp32", "512-fp64", "1024-fp32"])
+def test_pressure_of_taylor_green_at_full_size(dev, N, prec):
     """The Taylor-Green field has the closed-form pressure
     (cos 2x + cos 2y)(cos 2z + 2)/16 (pinned in the oracle at 16^3); the same
     field on the large grid must give the same coefficients, and nothing else."""
@@ -370,13 +371,14 @@ def test_pressure_of_taylor_green_at_full_size(dev, N):
     uh = np.array([O.fwd(u), O.fwd(v), O.fwd(np.zeros((n1,) * 3))])
     small = full_to_compact(np.concatenate([uh, np.zeros((1,) + uh.shape[1:], complex)]), n1)
     ref_small = full_to_compact(O.pressure_hat(uh, g)[None], n1)
-    p = B.Params(N=N, precision=B.FP32_MIXED)
+    p = B.Params(N=N, precision=prec)
     sim = B.Simulation(p, device=dev)
-    sim.set_state(torch.from_numpy(_embed(small, n1, N).astype(np.complex64)).to(dev))
+    big = _embed(small, n1, N)
+    sim.set_state(torch.from_numpy(big.astype(np.complex64) if prec == B.FP32_MIXED else big).to(dev))
     got = sim.pressure().cpu().numpy().astype(np.complex128)
     ref = _embed(ref_small, n1, N)[0]
     scale = np.abs(ref).max()
-    assert np.abs(got - ref).max() < 1e-6 * scale
+    assert np.abs(got - ref).max() < (1e-6 if prec == B.FP32_MIXED else 1e-12) * scale
     sim.close()
     torch.cuda.empty_cache()
 
