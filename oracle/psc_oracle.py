@@ -55,6 +55,9 @@ INTEG_RK4 = 1
 NL_ROTATIONAL = 0           # P(u x omega)
 NL_CONVECTIVE = 1           # -P((u.grad) u), the form the paper writes (section 2.3)
 
+DEALIAS_TWO_THIRDS = 0      # keep |k_i| <= (N-1)//3
+DEALIAS_PHASE_SHIFT = 1     # the paper's: keep |k| < sqrt(2) N / 3, phase-shifted products
+
 
 @dataclasses.dataclass
 class Params:
@@ -78,6 +81,7 @@ class Params:
     scalar_on: int = 1
     record_every: int = 10
     nonlinear_form: int = NL_ROTATIONAL
+    dealias: int = DEALIAS_TWO_THIRDS
 
     @property
     def D(self) -> float:
@@ -89,27 +93,45 @@ class Params:
 # Grid, wavenumbers and the DFT convention (Eqs. 4-5)
 # --------------------------------------------------------------------------
 
+def sphere_halfwidth(N: int) -> int:
+    """Largest integer k with k < sqrt(2) N / 3, i.e. 9 k^2 < 2 N^2."""
+    k = 0
+    while 9 * (k + 1) ** 2 < 2 * N * N:
+        k += 1
+    return k
+
+
 class Grid:
     """Periodic box of side 2*pi with N^3 points (Eq. 4) and its wavenumbers.
 
     ``kx, ky, kz`` are integer wavenumbers broadcastable against an
-    ``rfftn`` array; ``k2 = |k|^2``; ``mask`` is the 2/3-rule retained set;
-    ``w`` counts each stored mode together with its conjugate partner
-    (1 on the kx = 0 plane, 2 elsewhere)."""
+    ``rfftn`` array; ``k2 = |k|^2``; ``mask`` is the retained set: the 2/3-rule
+    cube |k_i| <= K = (N-1)//3, or (``dealias`` = DEALIAS_PHASE_SHIFT) the
+    paper's sphere |k| < sqrt(2) N / 3 (section 2.3), whose products are then
+    formed on the grid and on the grid shifted by half a cell (``shifts``);
+    ``w`` counts each stored mode together with its conjugate partner (1 on
+    the kx = 0 plane, 2 elsewhere)."""
 
-    def __init__(self, N: int):
+    def __init__(self, N: int, dealias: int = DEALIAS_TWO_THIRDS):
         if N < 8:
             raise ValueError("N must be at least 8")
         self.N = N
-        self.K = (N - 1) // 3
+        self.dealias = dealias
         kfull = np.fft.fftfreq(N, 1.0 / N).round().astype(np.int64)
         self.kz = kfull.reshape(N, 1, 1)
         self.ky = kfull.reshape(1, N, 1)
         self.kx = np.arange(N // 2 + 1, dtype=np.int64).reshape(1, 1, N // 2 + 1)
         self.k2 = self.kx ** 2 + self.ky ** 2 + self.kz ** 2
-        K = self.K
-        self.mask = ((np.abs(self.kx) <= K) & (np.abs(self.ky) <= K)
-                     & (np.abs(self.kz) <= K))
+        if dealias == DEALIAS_PHASE_SHIFT:
+            self.K = sphere_halfwidth(N)
+            self.mask = 9 * self.k2 < 2 * N * N
+            self.shifts = (0, 1)
+        else:
+            self.K = (N - 1) // 3
+            K = self.K
+            self.mask = ((np.abs(self.kx) <= K) & (np.abs(self.ky) <= K)
+                         & (np.abs(self.kz) <= K))
+            self.shifts = (0,)
         self.w = np.where(self.kx == 0, 1.0, 2.0) * np.ones((N, N, 1))
         self.dx = 2.0 * np.pi / N
         c = self.dx * np.arange(N)
@@ -120,6 +142,13 @@ class Grid:
     @property
     def kvec(self):
         return (self.kx, self.ky, self.kz)
+
+    def phase(self, shift: int):
+        """exp(i k.delta) with delta = shift * (pi/N)(1, 1, 1): a field sampled
+        at x + delta has the coefficients phase * u_hat (Patterson and Orszag
+        1971).  Averaging a product formed at shifts 0 and 1 cancels every
+        alias wrapped an odd number of times; the sphere removes the rest."""
+        return np.exp(1j * shift * (np.pi / self.N) * (self.kx + self.ky + self.kz))
 
     @property
     def shape_hat(self):
@@ -137,8 +166,22 @@ def inv(ah: np.ndarray, N: int) -> np.ndarray:
 
 
 def truncate(ah: np.ndarray, g: Grid) -> np.ndarray:
-    """2/3-rule dealiasing: zero every mode outside |k_i| <= K (section 2.3)."""
+    """Dealiasing: zero every mode outside the retained set (section 2.3)."""
     return np.where(g.mask, ah, 0.0)
+
+
+def dealiased_products(fields_hat, product, g: Grid):
+    """The transforms of product(*physical fields) on the retained set, the
+    fields given by their transforms: one evaluation on the grid (2/3 rule), or
+    the average of the evaluations on the grid and on the half-cell-shifted
+    grid (phase-shift dealiasing).  product returns a list of physical fields."""
+    acc = None
+    for s in g.shifts:
+        ph = g.phase(s)
+        phys = [inv(ph * fh, g.N) for fh in fields_hat]
+        outs = [np.conj(ph) * fwd(o) for o in product(*phys)]
+        acc = outs if acc is None else [a + b for a, b in zip(acc, outs)]
+    return [truncate(a / len(g.shifts), g) for a in acc]
 
 
 # --------------------------------------------------------------------------
@@ -176,24 +219,19 @@ def nonlinear_rotational(uh, g: Grid):
 
     The NS right-hand side of Eq. 7 without the viscous and forcing terms:
     -u.grad u = u x omega - grad(|u|^2/2), and the gradient is removed by P."""
-    u = velocity(uh, g)
-    om = [inv(c, g.N) for c in curl_hat(uh, g)]
-    cross = [u[1] * om[2] - u[2] * om[1],
-             u[2] * om[0] - u[0] * om[2],
-             u[0] * om[1] - u[1] * om[0]]
-    return project([truncate(fwd(c), g) for c in cross], g)
+    def cross(u1, u2, u3, w1, w2, w3):
+        return [u2 * w3 - u3 * w2, u3 * w1 - u1 * w3, u1 * w2 - u2 * w1]
+    return project(dealiased_products(list(uh) + list(curl_hat(uh, g)), cross, g), g)
 
 
 def nonlinear_convective(uh, g: Grid):
     """-P[(u.grad u)_hat] on R, the form the paper writes in Eqs. 6-7
     (velocity and its gradient transformed back separately, section 2.3)."""
-    u = velocity(uh, g)
-    out = []
-    for i in range(3):
-        gi = [inv(c, g.N) for c in grad_hat(uh[i], g)]
-        adv = u[0] * gi[0] + u[1] * gi[1] + u[2] * gi[2]
-        out.append(-truncate(fwd(adv), g))
-    return project(out, g)
+    grads = [c for i in range(3) for c in grad_hat(uh[i], g)]  # d_j u_i at 3 i + j
+
+    def adv(u1, u2, u3, *d):
+        return [-(u1 * d[3 * i] + u2 * d[3 * i + 1] + u3 * d[3 * i + 2]) for i in range(3)]
+    return project(dealiased_products(list(uh) + grads, adv, g), g)
 
 
 def pressure_hat(uh, g: Grid):
@@ -215,9 +253,9 @@ def pressure_hat(uh, g: Grid):
 def scalar_advection(uh, ph, g: Grid):
     """(u.grad phi)_hat on R (Eq. 8), formed in physical space from the
     inverse transforms of u_hat and i k phi_hat."""
-    u = velocity(uh, g)
-    gp = [inv(c, g.N) for c in grad_hat(ph, g)]
-    return truncate(fwd(u[0] * gp[0] + u[1] * gp[1] + u[2] * gp[2]), g)
+    def dot(u1, u2, u3, g1, g2, g3):
+        return [u1 * g1 + u2 * g2 + u3 * g3]
+    return dealiased_products(list(uh) + list(grad_hat(ph, g)), dot, g)[0]
 
 
 # --------------------------------------------------------------------------
@@ -367,7 +405,11 @@ def shell_index(g: Grid) -> np.ndarray:
     return np.floor(np.sqrt(g.k2.astype(np.float64)) + 0.5).astype(np.int64)
 
 
-def num_shells(N: int) -> int:
+def num_shells(N: int, dealias: int = DEALIAS_TWO_THIRDS) -> int:
+    """Shells n = 0 .. floor(|k|_max + 1/2) of the retained set."""
+    if dealias == DEALIAS_PHASE_SHIFT:
+        K = sphere_halfwidth(N)
+        return int(math.floor(math.sqrt(float(K * K)) + 0.5)) + 2
     K = (N - 1) // 3
     return int(math.floor(math.sqrt(3.0 * K * K) + 0.5)) + 1
 
@@ -377,7 +419,7 @@ def shell_sum(vals: np.ndarray, g: Grid) -> np.ndarray:
     n = np.broadcast_to(shell_index(g), g.shape_hat)
     v = np.where(g.mask, vals, 0.0)
     return np.bincount(n.ravel(), weights=np.broadcast_to(v, g.shape_hat).ravel(),
-                       minlength=num_shells(g.N))[: num_shells(g.N)]
+                       minlength=num_shells(g.N, g.dealias))[: num_shells(g.N, g.dealias)]
 
 
 def spectra(uh, ph, g: Grid):
@@ -599,7 +641,7 @@ def run(p: Params, nsteps: int, uh=None, ph=None, with_records: bool = True):
     at every step n with n % record_every == 0 and of the final state.  With
     the deterministic forcing the band energy of the starting state is held
     after every step."""
-    g = Grid(p.N)
+    g = Grid(p.N, p.dealias)
     if uh is None:
         uh, ph = init_field(g, p)
     dt = p.dt

@@ -553,3 +553,61 @@ def test_sparse_triad_rhs_matches_fft_rhs():
         seen[kz % N, ky % N, kx] = True
     # every mode the FFT path fills is one the triad sum found
     assert np.abs(np.where(seen[None], 0, ref)).max() < 1e-11 * scale
+
+
+# ---------------------------------------------------------------- phase-shift dealiasing
+
+def _sphere_field(g, seed):
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((g.N,) * 3)
+    return O.truncate(O.fwd(a), g)
+
+
+def _exact_product_on_grid(ah, bh, g):
+    """a*b computed on a 2N grid (no aliasing for modes below N/2), returned as
+    the N-grid transform restricted to the retained set."""
+    N, N2 = g.N, 2 * g.N
+    kf2 = np.fft.fftfreq(N2, 1.0 / N2).round().astype(np.int64)
+    big = [np.zeros((N2, N2, N2 // 2 + 1), dtype=complex) for _ in range(2)]
+    kz, ky, kx = np.nonzero(np.broadcast_to(g.mask, g.shape_hat))
+    wz = np.broadcast_to(g.kz, g.shape_hat)[kz, ky, kx]
+    wy = np.broadcast_to(g.ky, g.shape_hat)[kz, ky, kx]
+    for dst, src in zip(big, (ah, bh)):
+        dst[wz % N2, wy % N2, kx] = src[kz, ky, kx] * 8.0
+    p = O.fwd(O.inv(big[0], N2) * O.inv(big[1], N2))
+    out = np.zeros(g.shape_hat, dtype=complex)
+    out[kz, ky, kx] = p[wz % N2, wy % N2, kx] / 8.0
+    return out
+
+
+@pytest.mark.parametrize("N", [16, 24])
+def test_phase_shift_dealiasing_removes_every_alias(N):
+    # Patterson-Orszag: averaging the product formed on the grid and on the grid
+    # shifted by half a cell cancels the aliases wrapped an odd number of times;
+    # truncating to |k| < sqrt(2) N / 3 removes the rest, so the product of two
+    # fields on the sphere equals the exact (2N-grid) product on the sphere
+    g = O.Grid(N, O.DEALIAS_PHASE_SHIFT)
+    a, b = _sphere_field(g, 1), _sphere_field(g, 2)
+    got = O.dealiased_products([a, b], lambda x, y: [x * y], g)[0]
+    exact = _exact_product_on_grid(a, b, g)
+    scale = np.abs(exact).max()
+    assert np.abs(got - exact).max() < 1e-12 * scale
+    # one grid alone is not alias-free for this retained set
+    single = O.truncate(O.fwd(O.inv(a, N) * O.inv(b, N)), g)
+    assert np.abs(single - exact).max() > 1e-3 * scale
+    assert O.sphere_halfwidth(N) == max(k for k in range(N) if 9 * k * k < 2 * N * N)
+
+
+def test_phase_shift_galerkin_system_conserves_energy_and_forms_agree():
+    N = 16
+    g = O.Grid(N, O.DEALIAS_PHASE_SHIFT)
+    rng = np.random.default_rng(5)
+    uh = O.project([O.truncate(O.fwd(rng.standard_normal((N,) * 3)), g) for _ in range(3)], g)
+    uh = np.array(uh)
+    rot = O.nonlinear_rotational(uh, g)
+    conv = O.nonlinear_convective(uh, g)
+    scale = max(np.abs(c).max() for c in rot)
+    assert max(np.abs(a - b).max() for a, b in zip(rot, conv)) < 1e-11 * scale
+    e = sum(np.sum(g.w * np.real(np.conj(uh[c]) * rot[c])) for c in range(3))
+    escale = sum(np.sum(g.w * np.abs(uh[c]) * np.abs(rot[c])) for c in range(3))
+    assert abs(e) < 1e-12 * escale
