@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--long-run", action="store_true",
                     help="only run 256^3 FP32-mixed and FP64 side by side for 2000 steps and "
                          "print their statistical agreement")
+    ap.add_argument("--dealias-compare", action="store_true",
+                    help="only time 256^3 steps under the 2/3 rule and under phase-shift dealiasing "
+                         "(both precisions) and print steps/s and launches per step")
     return ap.parse_args()
 
 
@@ -370,6 +373,43 @@ def run_long(N=256, steps=2000, every=10):
     return out
 
 
+def run_dealias(N=256, every=10):
+    """Steps/s of the 2/3 rule and of phase-shift dealiasing (the sphere
+    |k| < sqrt(2) N/3, products averaged over the grid and the half-cell-shifted
+    grid) at N^3, FP32-mixed and FP64, CFL 0.5 with a record every 10 steps:
+    device time of the timed steps on the simulation's stream after warm-up."""
+    import torch
+    import paper_2012_04838_gb300 as psc
+    from paper_2012_04838_gb300.serve import nu_for_resolution
+    out = {"N": N, "record_every": every}
+    for pname, prec, steps in (("fp32_mixed", psc.FP32_MIXED, 20), ("fp64", psc.FP64, 10)):
+        for dname, dl in (("two_thirds", psc.DEALIAS_TWO_THIRDS), ("phase_shift", psc.DEALIAS_PHASE_SHIFT)):
+            p = psc.Params(N=N, precision=prec, nu=nu_for_resolution(N, 1.5), Sc=1.0, beta=1.0, kF=2.0,
+                           eps_inj=0.1, cfl=0.5, ic=psc.IC_SPECTRUM_K4, seed=3, ic_energy=1.5,
+                           record_every=every, dealias=dl)
+            sim = psc.Simulation(p, device="cuda:0")
+            sim.init_field()
+            sim.step(3)
+            st = sim.stream
+            n0 = sim.launch_count()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            st.synchronize()
+            e0.record(st)
+            sim.step(steps)
+            e1.record(st)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            rec, _, _ = sim.stats()
+            out[f"{pname}_{dname}"] = {"steps_per_s": steps / (ms / 1e3), "ms_per_step": ms / steps,
+                                       "steps": steps, "launches_per_step": (sim.launch_count() - n0) / steps,
+                                       "K_end": rec["K"], "eps_end": rec["eps"]}
+            sim.close()
+            torch.cuda.empty_cache()
+        out[f"{pname}_phase_shift_cost"] = (out[f"{pname}_phase_shift"]["ms_per_step"]
+                                            / out[f"{pname}_two_thirds"]["ms_per_step"])
+    return out
+
+
 def run_companion(N=512, steps=200, every=10):
     """FP32-mixed against FP64 at 512^3 from the same IC (the 1024^3 workload's
     spectrum, forcing, Sc and CFL 0.5, nu for k_max eta = 1.5): the largest relative
@@ -425,6 +465,9 @@ def main():
         return 0
     if a.companion:
         print(json.dumps({"companion_512": run_companion()}), flush=True)
+        return 0
+    if a.dealias_compare:
+        print(json.dumps({"dealias_256": run_dealias()}), flush=True)
         return 0
 
     import torch

@@ -20,7 +20,8 @@
  *     data to host memory synchronise that stream; the others are asynchronous.
  *   - Threads: one simulation must not be used from two host threads at once;
  *     distinct simulations are independent.
- *   - Spectral layout ("compact state"): with K = floor((N-1)/3) (2/3 rule),
+ *   - Spectral layout ("compact state"): with K = floor((N-1)/3) (2/3 rule;
+ *     with PSC_DEALIAS_PHASE_SHIFT the largest k with 9 k^2 < 2 N^2),
  *     P = 2K+1 and M = K+1, the state is four fields (u1, u2, u3, phi), each
  *     a [P][P][M] array of complex numbers (interleaved real, imaginary) with
  *     element [kz+K][ky+K][kx] holding the unnormalised Fourier coefficient
@@ -65,6 +66,16 @@ typedef enum { PSC_FORCE_NONE = 0, PSC_FORCE_CONST_POWER = 1, PSC_FORCE_HOLD_ENE
  * fields; a larger workspace).  The two agree to round-off on the retained set. */
 typedef enum { PSC_NL_ROTATIONAL = 0, PSC_NL_CONVECTIVE = 1 } psc_nonlinear;
 typedef enum { PSC_INTEG_IFRK4 = 0, PSC_INTEG_RK4 = 1 } psc_integrator;
+/* Dealiasing of the products (section 2.3).  TWO_THIRDS: the retained set is the
+ * cube |k_i| <= K = (N-1)/3, whose quadratic products are alias-free on one grid.
+ * PHASE_SHIFT: the paper's sphere |k| < sqrt(2) N / 3, stored in the cube of
+ * half-width K = the largest k with 9 k^2 < 2 N^2 (modes of that cube outside the
+ * sphere are zero); every product is formed on the grid and on the grid shifted
+ * by half a cell in each direction, and the two transforms are averaged, which
+ * cancels the aliases that the sphere alone leaves (Patterson and Orszag 1971).
+ * Twice the transforms of the right-hand side; built for N <= 256 (else
+ * PSC_EUNSUPPORTED_N); psc_pressure is not offered with it (PSC_EINVAL). */
+typedef enum { PSC_DEALIAS_TWO_THIRDS = 0, PSC_DEALIAS_PHASE_SHIFT = 1 } psc_dealias;
 
 /* Problem statement (Table 2 of the paper; Sc and beta from section 2.3).
  * Fields are plain values; zero-initialise and set what you need. */
@@ -88,6 +99,8 @@ typedef struct {
   double ic_noise_frac; /* Taylor-Green IC: noise energy as a fraction of 1/8         */
   int32_t scalar_on;    /* 0: phi is held at zero                                     */
   int32_t nonlinear_form; /* psc_nonlinear                                            */
+  int32_t dealias;        /* psc_dealias                                              */
+  int32_t reserved;       /* must be zero                                             */
 } psc_params;
 
 /* One statistics record of the current state (section 2.3): Table 1,

@@ -27,6 +27,7 @@ class CParams(ct.Structure):
         ("seed", ct.c_uint64), ("ic", ct.c_int32), ("record_every", ct.c_int32),
         ("ic_energy", ct.c_double), ("ic_noise_frac", ct.c_double),
         ("scalar_on", ct.c_int32), ("nonlinear_form", ct.c_int32),
+        ("dealias", ct.c_int32), ("reserved", ct.c_int32),
     ]
 
 
@@ -52,6 +53,7 @@ FP64, FP32_MIXED = 0, 1
 IC_SPECTRUM_K4, IC_TAYLOR_GREEN_NOISE, IC_PAPER_EQ9 = 0, 1, 2
 FORCE_NONE, FORCE_CONST_POWER, FORCE_HOLD_ENERGY = 0, 1, 2
 NL_ROTATIONAL, NL_CONVECTIVE = 0, 1
+DEALIAS_TWO_THIRDS, DEALIAS_PHASE_SHIFT = 0, 1
 INTEG_IFRK4, INTEG_RK4 = 0, 1
 
 # every entry point of include/psc.h: (name, restype, argtypes)
@@ -147,6 +149,7 @@ class Params:
     ic_noise_frac: float = 0.01
     scalar_on: int = 1
     nonlinear_form: int = 0  # NL_ROTATIONAL
+    dealias: int = 0  # DEALIAS_TWO_THIRDS
 
     def c(self) -> CParams:
         return CParams(**{f.name: getattr(self, f.name) for f in dataclasses.fields(self)})
@@ -167,8 +170,19 @@ def supported_sizes() -> list[int]:
     return list(buf[:n])
 
 
-def compact_shape(N: int):
-    K = (N - 1) // 3
+def retained_halfwidth(N: int, dealias: int = DEALIAS_TWO_THIRDS) -> int:
+    """K of the compact layout: (N-1)//3 (2/3 rule), or the largest k with
+    9 k^2 < 2 N^2 (the cube holding the sphere of phase-shift dealiasing)."""
+    if dealias == DEALIAS_PHASE_SHIFT:
+        k = 0
+        while 9 * (k + 1) ** 2 < 2 * N * N:
+            k += 1
+        return k
+    return (N - 1) // 3
+
+
+def compact_shape(N: int, dealias: int = DEALIAS_TWO_THIRDS):
+    K = retained_halfwidth(N, dealias)
     return (4, 2 * K + 1, 2 * K + 1, K + 1)
 
 
@@ -192,7 +206,7 @@ class Simulation:
             _check(self.lib, self.lib.psc_create(ct.byref(cp), ct.c_void_p(self._ws_ptr), nbytes,
                                                  ct.c_void_p(self.stream.cuda_stream), ct.byref(self._h)))
         self.cdtype = torch.complex128 if p.precision == FP64 else torch.complex64
-        self.shape = compact_shape(p.N)
+        self.shape = compact_shape(p.N, p.dealias)
 
     # -- lifecycle
     def close(self) -> None:
@@ -253,7 +267,7 @@ class Simulation:
     def pressure(self):
         """Modified pressure p_hat of the current state (Eq. 6), one compact
         field as a new device tensor [2K+1][2K+1][K+1]."""
-        K = (self.p.N - 1) // 3
+        K = retained_halfwidth(self.p.N, self.p.dealias)
         out = self.torch.empty((2 * K + 1, 2 * K + 1, K + 1), dtype=self.cdtype, device=self.device)
         _check(self.lib, self.lib.psc_pressure(self._h, ct.c_void_p(out.data_ptr()),
                                                out.numel() * out.element_size()))

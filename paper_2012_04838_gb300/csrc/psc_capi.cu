@@ -18,9 +18,11 @@
 
 // Grid sizes with compiled pass kernels (one object file per size and precision).
 #define PSC_SIZES(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(512) X(1024)
-#define PSC_DECL(n)                                  \
-  const psc::PassTable* psc_pass_table_float_##n();  \
-  const psc::PassTable* psc_pass_table_double_##n();
+#define PSC_DECL(n)                                     \
+  const psc::PassTable* psc_pass_table_float_##n();     \
+  const psc::PassTable* psc_pass_table_double_##n();    \
+  const psc::PassTable* psc_pass_table_ps_float_##n();  \
+  const psc::PassTable* psc_pass_table_ps_double_##n();
 PSC_SIZES(PSC_DECL)
 #undef PSC_DECL
 
@@ -37,6 +39,15 @@ const PassTable* table_f32(int N) {
 const PassTable* table_f64(int N) {
   switch (N) {
 #define PSC_CASE(n) case n: return psc_pass_table_double_##n();
+    PSC_SIZES(PSC_CASE)
+#undef PSC_CASE
+    default: return nullptr;
+  }
+}
+// phase-shift dealiasing (null where not built)
+const PassTable* table_ps(int N, bool fp64) {
+  switch (N) {
+#define PSC_CASE(n) case n: return fp64 ? psc_pass_table_ps_double_##n() : psc_pass_table_ps_float_##n();
     PSC_SIZES(PSC_CASE)
 #undef PSC_CASE
     default: return nullptr;
@@ -81,13 +92,15 @@ static psc_status cuda_fail(cudaError_t e, const char* where) {
 
 // ---------------------------------------------------------------- layout
 
-static int num_shells(int N) {
-  const int K = (N - 1) / 3;
-  return (int)std::floor(std::sqrt(3.0 * K * K) + 0.5) + 1;
+// Shells n = 0 .. floor(|k|_max + 1/2) of the retained set: the cube's corner
+// |k| = sqrt(3) K, or below sqrt(2) N / 3 for the sphere (at most K + 1).
+static int num_shells(const Dims& d) {
+  if (d.sph) return d.K + 2;
+  return (int)std::floor(std::sqrt(3.0 * d.K * d.K) + 0.5) + 1;
 }
 
 struct Layout {
-  size_t ctrl, U, V, Acc, zreg, yreg, tw, eu, ep, partials, shells, fac, total;
+  size_t ctrl, U, V, Acc, zreg, yreg, tw, eu, ep, partials, shells, fac, R0, phase, total;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -101,7 +114,7 @@ static Layout make_layout(const Dims& d, int fp64, int xwarps, int convective) {
   size_t yreg = (size_t)(convective ? Y_NSTREAM : Y_NSTREAM_ROT) * ys * cs;
   if (4 * zs * cs > yreg) yreg = 4 * zs * cs;
   if (3 * S * 16 > yreg) yreg = 3 * S * 16;  // FP64 scratch of the initial condition
-  const int nsh = num_shells(d.N);
+  const int nsh = num_shells(d);
   Layout L;
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
@@ -117,6 +130,9 @@ static Layout make_layout(const Dims& d, int fp64, int xwarps, int convective) {
   L.partials = take((size_t)xwarps * NQ * 8);
   L.shells = take((size_t)NSQ * nsh * 8);
   L.fac = take((size_t)nsh * 8);
+  // phase-shift dealiasing: the products of the unshifted grid, and the phases
+  L.R0 = take(d.sph ? 4 * S * cs : 0);
+  L.phase = take(d.sph ? (size_t)d.P * cs : 0);
   L.total = o;
   return L;
 }
@@ -203,6 +219,10 @@ static psc_status check_params(const psc_params* p) {
   if (p->nonlinear_form != PSC_NL_ROTATIONAL && p->nonlinear_form != PSC_NL_CONVECTIVE)
     return fail(PSC_EINVAL, "bad nonlinear_form");
   if (p->integrator != PSC_INTEG_IFRK4 && p->integrator != PSC_INTEG_RK4) return fail(PSC_EINVAL, "bad integrator");
+  if (p->dealias != PSC_DEALIAS_TWO_THIRDS && p->dealias != PSC_DEALIAS_PHASE_SHIFT)
+    return fail(PSC_EINVAL, "bad dealias");
+  if (p->dealias == PSC_DEALIAS_PHASE_SHIFT && !table_ps(p->N, p->precision == PSC_FP64))
+    return fail(PSC_EUNSUPPORTED_N, "phase-shift dealiasing is built for N <= 256, not N=" + std::to_string(p->N));
   if (p->ic < 0 || p->ic > 2) return fail(PSC_EINVAL, "bad ic");
   if (!(p->kF >= 0.0) || !(p->eps_inj >= 0.0)) return fail(PSC_EINVAL, "kF and eps_inj must be >= 0");
   if (!(p->ic_energy >= 0.0) || !(p->ic_noise_frac >= 0.0)) return fail(PSC_EINVAL, "IC energies must be >= 0");
@@ -210,8 +230,11 @@ static psc_status check_params(const psc_params* p) {
 }
 
 static const PassTable* pick_table(const psc_params* p) {
+  if (p->dealias == PSC_DEALIAS_PHASE_SHIFT) return table_ps(p->N, p->precision == PSC_FP64);
   return p->precision == PSC_FP64 ? table_f64(p->N) : table_f32(p->N);
 }
+
+static Dims dims_of(const psc_params* p) { return make_dims(p->N, p->dealias == PSC_DEALIAS_PHASE_SHIFT); }
 
 namespace {
 template <typename T> void launch_iftab(psc_sim* s);
@@ -233,7 +256,7 @@ psc_status psc_workspace_size(const psc_params* p, size_t* bytes) {
   if (s != PSC_OK) return s;
   if (!bytes) return fail(PSC_EINVAL, "null bytes");
   const PassTable* tb = pick_table(p);
-  *bytes = make_layout(make_dims(p->N), p->precision == PSC_FP64, tb->xwarps,
+  *bytes = make_layout(dims_of(p), p->precision == PSC_FP64, tb->xwarps,
                        p->nonlinear_form == PSC_NL_CONVECTIVE).total;
   return PSC_OK;
 }
@@ -244,7 +267,7 @@ psc_status psc_create(const psc_params* p, void* dev_ws, size_t ws_bytes, void* 
   if (!out || !dev_ws) return fail(PSC_EINVAL, "null workspace or output handle");
   if (((uintptr_t)dev_ws & 255) != 0) return fail(PSC_EINVAL, "workspace must be 256-byte aligned");
   const PassTable* tb = pick_table(p);
-  Layout L = make_layout(make_dims(p->N), p->precision == PSC_FP64, tb->xwarps,
+  Layout L = make_layout(dims_of(p), p->precision == PSC_FP64, tb->xwarps,
                          p->nonlinear_form == PSC_NL_CONVECTIVE);
   if (ws_bytes < L.total)
     return fail(PSC_ENOMEM_BUDGET, "workspace of " + std::to_string(ws_bytes) + " bytes < required " +
@@ -252,7 +275,7 @@ psc_status psc_create(const psc_params* p, void* dev_ws, size_t ws_bytes, void* 
   psc_sim* sim = new (std::nothrow) psc_sim();
   if (!sim) return fail(PSC_EINVAL, "host allocation failed");
   sim->p = *p;
-  sim->d = make_dims(p->N);
+  sim->d = dims_of(p);
   sim->fp64 = p->precision == PSC_FP64;
   sim->tb = tb;
   sim->st = (cudaStream_t)stream;
@@ -260,7 +283,7 @@ psc_status psc_create(const psc_params* p, void* dev_ws, size_t ws_bytes, void* 
   sim->L = L;
   sim->ctrl = (Ctrl*)(sim->ws + L.ctrl);
   sim->step = 0;
-  sim->nshell = num_shells(p->N);
+  sim->nshell = num_shells(sim->d);
   // twiddles, control block, zero state
   const int N = p->N;
   std::vector<double> twd(2 * (size_t)N);
@@ -274,6 +297,20 @@ psc_status psc_create(const psc_params* p, void* dev_ws, size_t ws_bytes, void* 
   cudaError_t e;
   if (sim->fp64) e = cudaMemcpyAsync(sim->ws + L.tw, twd.data(), twd.size() * 8, cudaMemcpyHostToDevice, sim->st);
   else e = cudaMemcpyAsync(sim->ws + L.tw, twf.data(), twf.size() * 4, cudaMemcpyHostToDevice, sim->st);
+  // phase factors exp(i k pi / N) = conj(exp(-2 pi i k / 2N)), k = -K..K
+  std::vector<double> phd(2 * (size_t)sim->d.P);
+  std::vector<float> phf(phd.size());
+  for (int k = -sim->d.K; k <= sim->d.K; ++k) {
+    double c, sn;
+    twiddle(k < 0 ? 2L * N + k : (long)k, 2L * N, &c, &sn);
+    phd[2 * (k + sim->d.K)] = c;
+    phd[2 * (k + sim->d.K) + 1] = -sn;
+  }
+  for (size_t i = 0; i < phd.size(); ++i) phf[i] = (float)phd[i];
+  if (e == cudaSuccess && sim->d.sph) {
+    if (sim->fp64) e = cudaMemcpyAsync(sim->ws + L.phase, phd.data(), phd.size() * 8, cudaMemcpyHostToDevice, sim->st);
+    else e = cudaMemcpyAsync(sim->ws + L.phase, phf.data(), phf.size() * 4, cudaMemcpyHostToDevice, sim->st);
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(sim->ctrl, &c0, sizeof(c0), cudaMemcpyHostToDevice, sim->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(sim->ws + L.U, 0, L.V - L.U, sim->st);
   if (e == cudaSuccess) {
@@ -378,6 +415,8 @@ PassArgs pass_args(psc_sim* s, const void* in) {
   a.partials = (double*)(s->ws + s->L.partials);
   a.ctrl = s->ctrl;
   a.want_umax = 0;
+  a.phase = s->ws + s->L.phase;
+  a.shift = 0;
   a.st = s->st;
   return a;
 }
@@ -403,6 +442,7 @@ CombineArgs combine_args(psc_sim* s, const void* vin) {
   CombineArgs c;
   c.d = s->d;
   c.rb = s->ws + s->L.zreg;
+  c.rb2 = s->d.sph ? (const void*)(s->ws + s->L.R0) : nullptr;
   c.vin = vin;
   c.U = s->ws + s->L.U;
   c.V = s->ws + s->L.V;
@@ -438,27 +478,34 @@ void launch_combine(psc_sim* s, int stage, const CombineArgs& c) {
 }
 
 // The five FFT passes of one RHS evaluation of `in`, leaving the unprojected
-// compact (NL, u.grad phi) in the z region.
+// compact (NL, u.grad phi) in the z region.  With phase-shift dealiasing the
+// products are formed twice, on the grid (into the R0 region) and on the grid
+// shifted by half a cell (into the z region); the combine averages them.
 template <typename T>
 void rhs_passes(psc_sim* s, const void* in, bool umax, bool step_start = false) {
-  PassArgs a = pass_args(s, in);
-  a.want_umax = umax ? 1 : 0;
   if (umax) cudaMemsetAsync(&s->ctrl->umax_bits, 0, sizeof(unsigned long long), s->st);
   launch_famp<T>(s, in, step_start);
   // the convective form takes the 8 z-stage streams of the statistics pass and
   // d_y u_z, d_z u_y separately at the y stage
   const bool conv = s->p.nonlinear_form == PSC_NL_CONVECTIVE;
-  launch(s, PSC_K_ZINV, 1, [&] { s->tb->zinv(a, conv, s->wv[SP_ZINV]); });
-  launch(s, PSC_K_YINV, 1, [&] { s->tb->yinv(a, conv ? YMODE_CONVECTIVE : YMODE_RHS, s->wv[SP_YINV]); });
-  launch(s, PSC_K_XPASS, 1, [&] { s->tb->xpass(a, conv ? XMODE_CONVECTIVE : XMODE_RHS); });
-  if (umax && s->p.cfl > 0.0) {
-    launch(s, PSC_K_OTHER, 1, [&] {
-      k_cfl<<<1, 32, 0, s->st>>>(s->ctrl, s->p.cfl, 2.0 * M_PI / s->p.N, s->p.record_every);
-    });
-    launch_iftab<T>(s);
+  const int nshift = s->d.sph ? 2 : 1;
+  for (int sh = 0; sh < nshift; ++sh) {
+    PassArgs a = pass_args(s, in);
+    a.shift = sh;
+    a.want_umax = umax && sh == 0 ? 1 : 0;
+    if (nshift == 2 && sh == 0) a.rb = s->ws + s->L.R0;
+    launch(s, PSC_K_ZINV, 1, [&] { s->tb->zinv(a, conv, s->wv[SP_ZINV]); });
+    launch(s, PSC_K_YINV, 1, [&] { s->tb->yinv(a, conv ? YMODE_CONVECTIVE : YMODE_RHS, s->wv[SP_YINV]); });
+    launch(s, PSC_K_XPASS, 1, [&] { s->tb->xpass(a, conv ? XMODE_CONVECTIVE : XMODE_RHS); });
+    if (a.want_umax && s->p.cfl > 0.0) {
+      launch(s, PSC_K_OTHER, 1, [&] {
+        k_cfl<<<1, 32, 0, s->st>>>(s->ctrl, s->p.cfl, 2.0 * M_PI / s->p.N, s->p.record_every);
+      });
+      launch_iftab<T>(s);
+    }
+    launch(s, PSC_K_YFWD, 1, [&] { s->tb->yfwd(a, s->wv[SP_YFWD]); });
+    launch(s, PSC_K_ZFWD, 1, [&] { s->tb->zfwd(a, s->wv[SP_ZFWD]); });
   }
-  launch(s, PSC_K_YFWD, 1, [&] { s->tb->yfwd(a, s->wv[SP_YFWD]); });
-  launch(s, PSC_K_ZFWD, 1, [&] { s->tb->zfwd(a, s->wv[SP_ZFWD]); });
 }
 
 template <typename T>
@@ -668,7 +715,7 @@ psc_status autotune(psc_sim* s) {
   }
   const char* env = std::getenv("PSC_TUNE");
   if (env && env[0] == '0') return PSC_OK;
-  const std::pair<int, int> key(N, s->fp64);
+  const std::pair<int, int> key(N, s->fp64 + 2 * s->d.sph);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -742,6 +789,7 @@ psc_status psc_rhs(psc_sim* s, const void* in, void* out) {
 psc_status psc_pressure(psc_sim* s, void* out, size_t bytes) {
   if (!s || !out) return fail(PSC_EINVAL, "null argument");
   if (bytes != (size_t)s->d.S * (s->fp64 ? 16 : 8)) return fail(PSC_EINVAL, "pressure buffer size mismatch");
+  if (s->d.sph) return fail(PSC_EINVAL, "the pressure is formed with the 2/3 rule only");
   return s->fp64 ? do_pressure<double>(s, out) : do_pressure<float>(s, out);
 }
 

@@ -21,15 +21,26 @@ constexpr int NSQ = 5;
 
 struct Dims {
   int N, K, M, P;
+  int sph;       // 1: retained set is the sphere 9|k|^2 < 2 N^2 inside the cube |k_i| <= K
   long long S;   // compact elements per field: P*P*M
   long long zs;  // one stream of the z-transformed stage: N*P*M
   long long ys;  // one stream of the y-transformed stage: N*N*M
 };
 
-inline Dims make_dims(int N) {
+// Largest integer k with k < sqrt(2) N / 3, i.e. 9 k^2 < 2 N^2: the half-width
+// of the cube that holds the sphere kept by phase-shift dealiasing (section 2.3).
+__host__ __device__ constexpr int sphere_halfwidth(int N) {
+  int k = 0;
+  while (9 * (k + 1) * (k + 1) < 2 * N * N) ++k;
+  return k;
+}
+
+// Retained half-width K: the 2/3 rule (N-1)/3, or the sphere's half-width.
+inline Dims make_dims(int N, int sph = 0) {
   Dims d;
   d.N = N;
-  d.K = (N - 1) / 3;
+  d.sph = sph ? 1 : 0;
+  d.K = sph ? sphere_halfwidth(N) : (N - 1) / 3;
   d.M = d.K + 1;
   d.P = 2 * d.K + 1;
   d.S = (long long)d.P * d.P * d.M;
@@ -69,6 +80,8 @@ struct PassArgs {
   double* partials; // X-pass statistics partials [xwarps][NQ]
   Ctrl* ctrl;
   int want_umax;    // X pass also reduces max |u1|+|u2|+|u3|
+  const void* phase; // exp(i k pi / N), k = -K..K (phase-shift dealiasing)
+  int shift;        // 1: evaluate on the grid shifted by half a cell
   cudaStream_t st;
 };
 

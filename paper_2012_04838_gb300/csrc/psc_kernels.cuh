@@ -10,6 +10,7 @@ namespace psc {
 struct CombineArgs {
   Dims d;
   const void* rb;     // unprojected (NL1, NL2, NL3, u.grad phi) in compact layout
+  const void* rb2;    // phase-shift dealiasing: the same on the unshifted grid (else null)
   const void* vin;    // stage input state
   void* U;            // state u_n (updated in place at stage 4)
   void* V;            // next stage input
@@ -29,6 +30,11 @@ __device__ __forceinline__ void mode_of(const Dims& d, long long i, int& kx, int
   const long long r = i / d.M;
   ky = (int)(r % d.P) - d.K;
   kz = (int)(r / d.P) - d.K;
+}
+
+// A mode of the cube outside the sphere 9|k|^2 < 2 N^2 when that is the retained set.
+__device__ __forceinline__ bool outside_sphere(const Dims& d, long long k2) {
+  return d.sph && 9 * k2 >= 2LL * d.N * d.N;
 }
 
 // STAGE 0: write the right-hand side N(v) to `out`.
@@ -55,7 +61,16 @@ __global__ void __launch_bounds__(256) k_combine(CombineArgs c) {
   const C* __restrict__ rb = static_cast<const C*>(c.rb);
   const C* __restrict__ vin = static_cast<const C*>(c.vin);
   C r0 = rb[i], r1 = rb[S + i], r2 = rb[2 * S + i];
-  const C r3 = rb[3 * S + i];
+  C r3 = rb[3 * S + i];
+  if (c.rb2) {
+    // phase-shift dealiasing: the mean of the products of the two grids
+    const C* __restrict__ rc = static_cast<const C*>(c.rb2);
+    const C q0 = rc[i], q1 = rc[S + i], q2 = rc[2 * S + i], q3 = rc[3 * S + i];
+    r0 = mk(T(0.5) * (q0.x + r0.x), T(0.5) * (q0.y + r0.y));
+    r1 = mk(T(0.5) * (q1.x + r1.x), T(0.5) * (q1.y + r1.y));
+    r2 = mk(T(0.5) * (q2.x + r2.x), T(0.5) * (q2.y + r2.y));
+    r3 = mk(T(0.5) * (q3.x + r3.x), T(0.5) * (q3.y + r3.y));
+  }
   // Leray projection (Eq. 7): r - k (k.r)/|k|^2; the k = 0 mode carries no velocity
   if (k2 > 0) {
     const T ik2 = T(1) / T(k2);
@@ -85,6 +100,10 @@ __global__ void __launch_bounds__(256) k_combine(CombineArgs c) {
   if (c.scalar_on) {
     const T b = (T)c.beta;
     rp = mk(-r3.x - b * v1.x, -r3.y - b * v1.y);
+  }
+  if (outside_sphere(d, k2)) {
+    // not retained: no tendency (the state is zero there)
+    r0 = r1 = r2 = rp = zero;
   }
   T E1u = T(1), E1p = T(1);
   if (c.integrator == 1) {
@@ -398,7 +417,7 @@ __global__ void k_ic_draw(Dims d, unsigned long long seed, double2* z) {
     re[c] = r * co;
     im[c] = r * s;
   }
-  if (k2 == 0) {
+  if (k2 == 0 || outside_sphere(d, k2)) {
     for (int c = 0; c < 3; ++c) z[c * d.S + i] = make_double2(0.0, 0.0);
     return;
   }
@@ -445,7 +464,7 @@ __global__ void k_ic_finish(Dims d, const double2* z, const double* fac, int tay
   const long long k2 = (long long)kx * kx + (long long)ky * ky + (long long)kz * kz;
   long long n = isqrt_floor(k2);
   if (k2 > n * n + n) ++n;
-  const double f = fac[n];
+  const double f = outside_sphere(d, k2) ? 0.0 : fac[n];
   double v[3][2];
   for (int c = 0; c < 3; ++c) {
     const double2 q = z[c * d.S + i];

@@ -72,8 +72,8 @@ __device__ __forceinline__ typename CT<T>::type* strided_twiddles(unsigned char*
 // Inputs n1 of the first DFT of an inverse (zero-padded) line that are zero
 // for every n2: positions R2 n1 + n2 all lie in the band K < p < N - K.  The
 // codelet generator emits DftZ<R1, +1, Z0, Z1> for exactly this range.
-template <int N> struct ZeroInputs {
-  static constexpr int R1 = PlanD<N>::R1, R2 = PlanD<N>::R2, K = (N - 1) / 3;
+template <int N, int KK = (N - 1) / 3> struct ZeroInputs {
+  static constexpr int R1 = PlanD<N>::R1, R2 = PlanD<N>::R2, K = KK;
   __host__ __device__ static constexpr bool zero(int n1) { return R2 * n1 > K && R2 * n1 + R2 - 1 < N - K; }
   __host__ __device__ static constexpr int first() {
     for (int n1 = 0; n1 < R1; ++n1)
@@ -90,23 +90,24 @@ template <int N> struct ZeroInputs {
 };
 
 // First DFT of a line: the pruned codelet for an inverse pass, else the full one.
-template <typename T, int N, int DIR, class C> __device__ __forceinline__ void first_dft(C (&a)[PlanD<N>::R1]) {
-  if constexpr (DIR > 0 && ZeroInputs<N>::ANY)
-    DftZ<PlanD<N>::R1, DIR, ZeroInputs<N>::Z0, ZeroInputs<N>::Z1>::template run<T, C>(a);
+template <typename T, int N, int DIR, int KK = (N - 1) / 3, class C>
+__device__ __forceinline__ void first_dft(C (&a)[PlanD<N>::R1]) {
+  if constexpr (DIR > 0 && ZeroInputs<N, KK>::ANY)
+    DftZ<PlanD<N>::R1, DIR, ZeroInputs<N, KK>::Z0, ZeroInputs<N, KK>::Z1>::template run<T, C>(a);
   else
     Dft<PlanD<N>::R1, DIR>::template run<T, C>(a);
 }
 
 // True if no output k1 + R1 k2 (k1 < R1) of a length-N line is a retained
 // wavenumber (K < k < N - K): a forward pass need not compute it.
-template <int N> __host__ __device__ constexpr bool dead_k2(int k2) {
-  return PlanD<N>::R1 * k2 > (N - 1) / 3 && PlanD<N>::R1 * k2 + PlanD<N>::R1 - 1 < N - (N - 1) / 3;
+template <int N, int KK = (N - 1) / 3> __host__ __device__ constexpr bool dead_k2(int k2) {
+  return PlanD<N>::R1 * k2 > KK && PlanD<N>::R1 * k2 + PlanD<N>::R1 - 1 < N - KK;
 }
 
 // One length-N DFT per column, direction DIR (-1 forward, +1 inverse).
 // ld(p) returns the element at line position p; st(k, v) stores output k.
 // A forward transform only computes the outputs a truncated pass can keep.
-template <typename T, int N, int W, int DIR, class LD, class ST>
+template <typename T, int N, int W, int DIR, int KK = (N - 1) / 3, class LD, class ST>
 __device__ __forceinline__ void strided_fft(const LD& ld, const ST& st,
                                             typename CT<T>::type* sm,
                                             const typename CT<T>::type* twsm,
@@ -121,10 +122,10 @@ __device__ __forceinline__ void strided_fft(const LD& ld, const ST& st,
     C a[R1];
     static_for<0, R1>([&](auto nc) {
       constexpr int n1 = decltype(nc)::value;
-      if constexpr (DIR > 0 && ZeroInputs<N>::zero(n1)) a[n1] = mk(T(0), T(0));  // not read
+      if constexpr (DIR > 0 && ZeroInputs<N, KK>::zero(n1)) a[n1] = mk(T(0), T(0));  // not read
       else a[n1] = ld(R2 * n1 + n2);
     });
-    first_dft<T, N, DIR>(a);
+    first_dft<T, N, DIR, KK>(a);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       C v = a[k1];
@@ -145,7 +146,7 @@ __device__ __forceinline__ void strided_fft(const LD& ld, const ST& st,
     Dft<R2, DIR>::template run<T, C>(b);
     static_for<0, R2>([&](auto kc) {
       constexpr int k2 = decltype(kc)::value;
-      if constexpr (!(DIR < 0 && dead_k2<N>(k2))) st(k1 + R1 * k2, b[k2]);
+      if constexpr (!(DIR < 0 && dead_k2<N, KK>(k2))) st(k1 + R1 * k2, b[k2]);
     });
   }
   __syncthreads();
@@ -153,21 +154,35 @@ __device__ __forceinline__ void strided_fft(const LD& ld, const ST& st,
 
 // wavenumber of line position p of a zero-padded / truncated axis; false if
 // the position is outside |k| <= K
-template <int N> __device__ __forceinline__ bool k_of_pos(int p, int& k) {
-  constexpr int K = (N - 1) / 3;
+template <int N, int KK = (N - 1) / 3> __device__ __forceinline__ bool k_of_pos(int p, int& k) {
+  constexpr int K = KK;
   if (p <= K) { k = p; return true; }
   if (p >= N - K) { k = p - N; return true; }
   return false;
 }
 
+// Multiply by the phase exp(+-i k pi / N) of wavenumber k (table a.phase,
+// index k + KK) when SHIFT: the spectra of fields sampled on the grid shifted
+// by half a cell (phase-shift dealiasing); identity otherwise.
+template <bool SHIFT, int KK, class C>
+__device__ __forceinline__ C shift_in(C v, const void* phase, int k) {
+  if constexpr (SHIFT) return cmul(v, static_cast<const C*>(phase)[k + KK]);
+  else return v;
+}
+template <bool SHIFT, int KK, class C>
+__device__ __forceinline__ C shift_out(C v, const void* phase, int k) {
+  if constexpr (SHIFT) return cmulc(v, static_cast<const C*>(phase)[k + KK]);
+  else return v;
+}
+
 // Each kernel runs its transforms through one copy of the transform code (a
 // runtime loop over its stream table), so the instruction footprint stays that
 // of a single two-step FFT however many streams the pass carries.
-template <typename T, int N, bool STATS, int W>
+template <typename T, int N, bool STATS, int W, int KK = (N - 1) / 3, bool SHIFT = false>
 __global__ void __launch_bounds__(StridedCfg<T, N, W>::THREADS, StridedCfg<T, N, W>::MINB)
 k_zinv(PassArgs a) {
   using C = typename CT<T>::type;
-  constexpr int K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
+  constexpr int K = KK, M = KK + 1, P = 2 * KK + 1;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int w = threadIdx.x, t = threadIdx.y;
@@ -196,13 +211,13 @@ k_zinv(PassArgs a) {
       default: f = 2; deriv = true; s = Z_DZUZ; break;
     }
     const C* __restrict__ src = in + f * S + (long long)iy * M + ix;
-    strided_fft<T, N, W, +1>(
+    strided_fft<T, N, W, +1, KK>(
         [&](int p) -> C {
           int kz;
-          if (!act || !k_of_pos<N>(p, kz)) return zero;
+          if (!act || !k_of_pos<N, KK>(p, kz)) return zero;
           const long long off = (long long)(kz + K) * P * M;
           if (!PSC_OK_INDEX(f * S + off + (long long)iy * M + ix, 4 * S, a.ctrl)) return zero;
-          const C v = src[off];
+          const C v = shift_in<SHIFT, KK>(src[off], a.phase, kz);
           return deriv ? mul_ik(v, T(kz)) : v;
         },
         [&](int z, C v) {
@@ -214,11 +229,11 @@ k_zinv(PassArgs a) {
   }
 }
 
-template <typename T, int N, int YM, int W>
+template <typename T, int N, int YM, int W, int KK = (N - 1) / 3, bool SHIFT = false>
 __global__ void __launch_bounds__(StridedCfg<T, N, W>::THREADS, StridedCfg<T, N, W>::MINB)
 k_yinv(PassArgs a) {
   using C = typename CT<T>::type;
-  constexpr int K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
+  constexpr int K = KK, M = KK + 1, P = 2 * KK + 1;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int w = threadIdx.x, t = threadIdx.y;
@@ -251,18 +266,18 @@ k_yinv(PassArgs a) {
       default: kind = 0; s1 = Z_DZUY; so = Y_DZUY; break;
     }
     const long long rowz = (long long)z * P * M + ix;
-    strided_fft<T, N, W, +1>(
+    strided_fft<T, N, W, +1, KK>(
         [&](int p) -> C {
           int ky;
-          if (!act || !k_of_pos<N>(p, ky)) return zero;
+          if (!act || !k_of_pos<N, KK>(p, ky)) return zero;
           const long long o = rowz + (long long)(ky + K) * M;
           if (!PSC_OK_INDEX(s1 * zs + o, (long long)Z_NSTREAM * zs, a.ctrl)) return zero;
-          const C v1 = zb[s1 * zs + o];
+          const C v1 = shift_in<SHIFT, KK>(zb[s1 * zs + o], a.phase, ky);
           if (kind == 0) return v1;
           const C d = mul_ik(v1, T(ky));
           if (kind == 1) return d;
           if (!PSC_OK_INDEX(s2 * zs + o, (long long)Z_NSTREAM * zs, a.ctrl)) return zero;
-          return csub(d, zb[s2 * zs + o]);
+          return csub(d, shift_in<SHIFT, KK>(zb[s2 * zs + o], a.phase, ky));
         },
         [&](int y, C v) {
           if (!act) return;
@@ -273,11 +288,11 @@ k_yinv(PassArgs a) {
   }
 }
 
-template <typename T, int N, int W>
+template <typename T, int N, int W, int KK = (N - 1) / 3, bool SHIFT = false>
 __global__ void __launch_bounds__(StridedCfg<T, N, W>::THREADS, StridedCfg<T, N, W>::MINB)
 k_yfwd(PassArgs a) {
   using C = typename CT<T>::type;
-  constexpr int K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
+  constexpr int K = KK, M = KK + 1, P = 2 * KK + 1;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int w = threadIdx.x, t = threadIdx.y;
@@ -291,7 +306,7 @@ k_yfwd(PassArgs a) {
   const C zero = mk(T(0), T(0));
 #pragma unroll 1
   for (int s = 0; s < 4; ++s) {
-    strided_fft<T, N, W, -1>(
+    strided_fft<T, N, W, -1, KK>(
         [&](int y) -> C {
           if (!act) return zero;
           const long long idx = s * ys + ((long long)z * N + y) * M + ix;
@@ -300,19 +315,19 @@ k_yfwd(PassArgs a) {
         },
         [&](int k, C v) {
           int ky;
-          if (!act || !k_of_pos<N>(k, ky)) return;
+          if (!act || !k_of_pos<N, KK>(k, ky)) return;
           const long long idx = s * zs + ((long long)z * P + (ky + K)) * M + ix;
-          if (PSC_OK_INDEX(idx, 4 * zs, a.ctrl)) yf[idx] = v;
+          if (PSC_OK_INDEX(idx, 4 * zs, a.ctrl)) yf[idx] = shift_out<SHIFT, KK>(v, a.phase, ky);
         },
         sm, tw, t, w);
   }
 }
 
-template <typename T, int N, int W>
+template <typename T, int N, int W, int KK = (N - 1) / 3, bool SHIFT = false>
 __global__ void __launch_bounds__(StridedCfg<T, N, W>::THREADS, StridedCfg<T, N, W>::MINB)
 k_zfwd(PassArgs a) {
   using C = typename CT<T>::type;
-  constexpr int K = PlanD<N>::K, M = PlanD<N>::M, P = PlanD<N>::P;
+  constexpr int K = KK, M = KK + 1, P = 2 * KK + 1;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int w = threadIdx.x, t = threadIdx.y;
@@ -326,7 +341,7 @@ k_zfwd(PassArgs a) {
   const C zero = mk(T(0), T(0));
 #pragma unroll 1
   for (int s = 0; s < 4; ++s) {
-    strided_fft<T, N, W, -1>(
+    strided_fft<T, N, W, -1, KK>(
         [&](int z) -> C {
           if (!act) return zero;
           const long long idx = s * zs + ((long long)z * P + iy) * M + ix;
@@ -335,9 +350,9 @@ k_zfwd(PassArgs a) {
         },
         [&](int k, C v) {
           int kz;
-          if (!act || !k_of_pos<N>(k, kz)) return;
+          if (!act || !k_of_pos<N, KK>(k, kz)) return;
           const long long idx = s * S + ((long long)(kz + K) * P + iy) * M + ix;
-          if (PSC_OK_INDEX(idx, 4 * S, a.ctrl)) rb[idx] = v;
+          if (PSC_OK_INDEX(idx, 4 * S, a.ctrl)) rb[idx] = shift_out<SHIFT, KK>(v, a.phase, kz);
         },
         sm, tw, t, w);
   }
@@ -373,15 +388,16 @@ template <typename T, int N> struct XCfg {
 // conj(X1[N-p]) + i conj(X2[N-p]) (p >= N-K), 0 elsewhere.  On return
 // z[j][k2] holds scale * IDFT(Z) at position (t + j TPL) + R1 k2, whose real
 // and imaginary parts are the two real fields.
-template <typename T, int N, class SPEC>
+template <typename T, int N, int KK = (N - 1) / 3, bool SHIFT = false, class SPEC>
 __device__ __forceinline__ void xinv(const SPEC& spec,
                                      typename CT<T>::type (&z)[PlanD<N>::J2][PlanD<N>::R2],
                                      typename CT<T>::type* ex,
-                                     const typename CT<T>::type* tw, int t, T scale) {
+                                     const typename CT<T>::type* tw, int t, T scale,
+                                     const void* phase = nullptr) {
   using C = typename CT<T>::type;
   using PL = PlanD<N>;
   using XC = XCfg<T, N>;
-  constexpr int R1 = PL::R1, R2 = PL::R2, TPL = PL::TPL, K = PL::K;
+  constexpr int R1 = PL::R1, R2 = PL::R2, TPL = PL::TPL, K = KK;
 #pragma unroll
   for (int j = 0; j < PL::J1; ++j) {
     const int n2 = t + j * TPL;
@@ -392,10 +408,14 @@ __device__ __forceinline__ void xinv(const SPEC& spec,
       C x1, x2;
       if (p <= K) {
         spec(p, x1, x2);
+        x1 = shift_in<SHIFT, KK>(x1, phase, p);
+        x2 = shift_in<SHIFT, KK>(x2, phase, p);
         if (p == 0) { x1.y = T(0); x2.y = T(0); }
         a[n1] = mk(x1.x - x2.y, x1.y + x2.x);
       } else if (p >= N - K) {
         spec(N - p, x1, x2);
+        x1 = shift_in<SHIFT, KK>(x1, phase, N - p);
+        x2 = shift_in<SHIFT, KK>(x2, phase, N - p);
         a[n1] = mk(x1.x + x2.y, x2.x - x1.y);
       } else {
         a[n1] = mk(T(0), T(0));
@@ -425,14 +445,14 @@ __device__ __forceinline__ void xinv(const SPEC& spec,
 // Forward DFT of a row holding two real fields packed as x1 + i x2 at the
 // positions xinv leaves them in; out(kx, X1, X2) receives both half spectra
 // for kx <= K: X1 = (Z[k] + conj Z[N-k])/2, X2 = (Z[k] - conj Z[N-k])/(2i).
-template <typename T, int N, class OUT>
+template <typename T, int N, int KK = (N - 1) / 3, bool SHIFT = false, class OUT>
 __device__ __forceinline__ void xfwd(typename CT<T>::type (&x)[PlanD<N>::J2][PlanD<N>::R2],
                                      const OUT& out, typename CT<T>::type* ex,
-                                     const typename CT<T>::type* tw, int t) {
+                                     const typename CT<T>::type* tw, int t, const void* phase = nullptr) {
   using C = typename CT<T>::type;
   using PL = PlanD<N>;
   using XC = XCfg<T, N>;
-  constexpr int R1 = PL::R1, R2 = PL::R2, TPL = PL::TPL, K = PL::K;
+  constexpr int R1 = PL::R1, R2 = PL::R2, TPL = PL::TPL, K = KK;
   // transposed plan: n = R1 n1' + n2' with n2' = t + j TPL < R1, n1' < R2
 #pragma unroll
   for (int j = 0; j < PL::J2; ++j) {
@@ -465,8 +485,8 @@ __device__ __forceinline__ void xfwd(typename CT<T>::type (&x)[PlanD<N>::J2][Pla
   for (int kx = t; kx <= K; kx += TPL) {
     const C A = ex[kx];
     const C B = ex[kx == 0 ? 0 : N - kx];
-    out(kx, mk(T(0.5) * (A.x + B.x), T(0.5) * (A.y - B.y)),
-        mk(T(0.5) * (A.y + B.y), T(0.5) * (B.x - A.x)));
+    out(kx, shift_out<SHIFT, KK>(mk(T(0.5) * (A.x + B.x), T(0.5) * (A.y - B.y)), phase, kx),
+        shift_out<SHIFT, KK>(mk(T(0.5) * (A.y + B.y), T(0.5) * (B.x - A.x)), phase, kx));
   }
   __syncwarp();
 }
@@ -475,13 +495,13 @@ __device__ __forceinline__ void umax_update(Ctrl* c, double v) {
   atomicMax(&c->umax_bits, (unsigned long long)__double_as_longlong(v));
 }
 
-template <typename T, int N, int MODE>
+template <typename T, int N, int MODE, int KK = (N - 1) / 3, bool SHIFT = false>
 __global__ void __launch_bounds__(32 * XCfg<T, N>::WARPS)
 k_xpass(PassArgs a) {
   using C = typename CT<T>::type;
   using PL = PlanD<N>;
   using XC = XCfg<T, N>;
-  constexpr int R1 = PL::R1, R2 = PL::R2, TPL = PL::TPL, J2 = PL::J2, M = PL::M;
+  constexpr int R1 = PL::R1, R2 = PL::R2, TPL = PL::TPL, J2 = PL::J2, M = KK + 1;
   constexpr int LPW = XC::LPW;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -532,7 +552,7 @@ k_xpass(PassArgs a) {
         else return c == 0 ? ux[j][k2] : (c == 1 ? uy[j][k2] : uz[j][k2]);
       };
       // (u1, u2)
-      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UY, kx); }, z, ex, tw, t, scale);
+      xinv<T, N, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UY, kx); }, z, ex, tw, t, scale, a.phase);
 #pragma unroll
       for (int j = 0; j < J2; ++j)
 #pragma unroll
@@ -546,7 +566,7 @@ k_xpass(PassArgs a) {
           }
         }
       // (u3, omega_1)
-      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UZ, kx); x2 = Y(Y_WX, kx); }, z, ex, tw, t, scale);
+      xinv<T, N, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UZ, kx); x2 = Y(Y_WX, kx); }, z, ex, tw, t, scale, a.phase);
 #pragma unroll
       for (int j = 0; j < J2; ++j)
 #pragma unroll
@@ -559,12 +579,12 @@ k_xpass(PassArgs a) {
           if (a.want_umax) um = max_keep_nan(um, fabs(getu(0, j, k2)) + fabs(getu(1, j, k2)) + fabs(u3));
         }
       // (omega_2, omega_3):  omega_2 = d_z u_1 - i kx u_3,  omega_3 = i kx u_2 - d_y u_1
-      xinv<T, N>(
+      xinv<T, N, KK, SHIFT>(
           [&](int kx, C& x1, C& x2) {
             x1 = csub(Y(Y_DZUX, kx), mul_ik(Y(Y_UZ, kx), T(kx)));
             x2 = csub(mul_ik(Y(Y_UY, kx), T(kx)), Y(Y_DYUX, kx));
           },
-          z, ex, tw, t, scale);
+          z, ex, tw, t, scale, a.phase);
 #pragma unroll
       for (int j = 0; j < J2; ++j)
 #pragma unroll
@@ -580,7 +600,7 @@ k_xpass(PassArgs a) {
       for (int j = 0; j < J2; ++j)
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) z[j][k2] = mk(nlx[j][k2], nly[j][k2]);
-      xfwd<T, N>(z,
+      xfwd<T, N, KK, SHIFT>(z,
                  [&](int kx, C X1, C X2) {
                    if (!valid) return;
                    const long long i0 = line * M + kx;
@@ -589,7 +609,7 @@ k_xpass(PassArgs a) {
                      xb[ys + i0] = X2;
                    }
                  },
-                 ex, tw, t);
+                 ex, tw, t, a.phase);
       if constexpr (MODE == XMODE_PRESSURE) {
         // (NL3, |u|^2 / 2): the inputs of the modified pressure
 #pragma unroll
@@ -599,7 +619,7 @@ k_xpass(PassArgs a) {
             const T u1 = getu(0, j, k2), u2 = getu(1, j, k2), u3 = getu(2, j, k2);
             z[j][k2] = mk(nlz[j][k2], T(0.5) * (u1 * u1 + u2 * u2 + u3 * u3));
           }
-        xfwd<T, N>(z,
+        xfwd<T, N, KK, SHIFT>(z,
                    [&](int kx, C X1, C X2) {
                      if (!valid) return;
                      const long long i0 = line * M + kx;
@@ -608,19 +628,19 @@ k_xpass(PassArgs a) {
                        xb[3 * ys + i0] = X2;
                      }
                    },
-                   ex, tw, t);
+                   ex, tw, t, a.phase);
         continue;
       }
       // (dphi/dx1, dphi/dx2)
-      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_PHI, kx), T(kx)); x2 = Y(Y_DYPHI, kx); },
-                 z, ex, tw, t, scale);
+      xinv<T, N, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_PHI, kx), T(kx)); x2 = Y(Y_DYPHI, kx); },
+                 z, ex, tw, t, scale, a.phase);
 #pragma unroll
       for (int j = 0; j < J2; ++j)
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2)
           sv[j][k2] = getu(0, j, k2) * z[j][k2].x + getu(1, j, k2) * z[j][k2].y;
       // (dphi/dx3, 0)
-      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZPHI, kx); x2 = zero; }, z, ex, tw, t, scale);
+      xinv<T, N, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZPHI, kx); x2 = zero; }, z, ex, tw, t, scale, a.phase);
 #pragma unroll
       for (int j = 0; j < J2; ++j)
 #pragma unroll
@@ -629,7 +649,7 @@ k_xpass(PassArgs a) {
           z[j][k2] = mk(nlz[j][k2], sv[j][k2]);
         }
       // forward (NL3, u.grad phi)
-      xfwd<T, N>(z,
+      xfwd<T, N, KK, SHIFT>(z,
                  [&](int kx, C X1, C X2) {
                    if (!valid) return;
                    const long long i0 = line * M + kx;
@@ -638,7 +658,7 @@ k_xpass(PassArgs a) {
                      xb[3 * ys + i0] = X2;
                    }
                  },
-                 ex, tw, t);
+                 ex, tw, t, a.phase);
     } else if constexpr (MODE == XMODE_CONVECTIVE) {
       // -(u.grad)u and u.grad phi from u, its nine gradients and grad phi; with
       // this stream set Y_WX holds d_y u_z and Y_DZUY holds d_z u_y
@@ -667,14 +687,14 @@ k_xpass(PassArgs a) {
         };
       };
       // (u1, u2)
-      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UY, kx); }, z, ex, tw, t, scale);
+      xinv<T, N, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UY, kx); }, z, ex, tw, t, scale, a.phase);
 #pragma unroll
       for (int j = 0; j < J2; ++j)
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) { putu(0, j, k2, z[j][k2].x); putu(1, j, k2, z[j][k2].y); }
       // (u3, d1 u1)
-      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UZ, kx); x2 = mul_ik(Y(Y_UX, kx), T(kx)); }, z, ex, tw, t,
-                 scale);
+      xinv<T, N, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UZ, kx); x2 = mul_ik(Y(Y_UX, kx), T(kx)); }, z, ex, tw, t,
+                 scale, a.phase);
 #pragma unroll
       for (int j = 0; j < J2; ++j)
 #pragma unroll
@@ -684,21 +704,21 @@ k_xpass(PassArgs a) {
           if (a.want_umax) um = max_keep_nan(um, fabs(getu(0, j, k2)) + fabs(getu(1, j, k2)) + fabs(z[j][k2].x));
         }
       // (d2 u1, d3 u1): aa = (u.grad) u1
-      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DYUX, kx); x2 = Y(Y_DZUX, kx); }, z, ex, tw, t, scale);
+      xinv<T, N, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DYUX, kx); x2 = Y(Y_DZUX, kx); }, z, ex, tw, t, scale, a.phase);
 #pragma unroll
       for (int j = 0; j < J2; ++j)
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) aa[j][k2] += getu(1, j, k2) * z[j][k2].x + getu(2, j, k2) * z[j][k2].y;
       // (d1 u2, d2 u2)
-      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_UY, kx), T(kx)); x2 = Y(Y_DYUY, kx); }, z, ex, tw, t,
-                 scale);
+      xinv<T, N, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_UY, kx), T(kx)); x2 = Y(Y_DYUY, kx); }, z, ex, tw, t,
+                 scale, a.phase);
 #pragma unroll
       for (int j = 0; j < J2; ++j)
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) bb[j][k2] = getu(0, j, k2) * z[j][k2].x + getu(1, j, k2) * z[j][k2].y;
       // (d3 u2, d1 u3): bb = (u.grad) u2; aa starts (u.grad) u3
-      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZUY, kx); x2 = mul_ik(Y(Y_UZ, kx), T(kx)); }, z, ex, tw, t,
-                 scale);
+      xinv<T, N, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZUY, kx); x2 = mul_ik(Y(Y_UZ, kx), T(kx)); }, z, ex, tw, t,
+                 scale, a.phase);
 #pragma unroll
       for (int j = 0; j < J2; ++j)
 #pragma unroll
@@ -707,28 +727,28 @@ k_xpass(PassArgs a) {
           z[j][k2] = mk(-aa[j][k2], -b2);  // (NL1, NL2)
           aa[j][k2] = c3;
         }
-      xfwd<T, N>(z, store(0), ex, tw, t);
+      xfwd<T, N, KK, SHIFT>(z, store(0), ex, tw, t, a.phase);
       // (d2 u3, d3 u3): aa = (u.grad) u3
-      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_WX, kx); x2 = Y(Y_DZUZ, kx); }, z, ex, tw, t, scale);
+      xinv<T, N, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_WX, kx); x2 = Y(Y_DZUZ, kx); }, z, ex, tw, t, scale, a.phase);
 #pragma unroll
       for (int j = 0; j < J2; ++j)
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) aa[j][k2] += getu(1, j, k2) * z[j][k2].x + getu(2, j, k2) * z[j][k2].y;
       // (dphi/dx1, dphi/dx2)
-      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_PHI, kx), T(kx)); x2 = Y(Y_DYPHI, kx); }, z, ex, tw, t,
-                 scale);
+      xinv<T, N, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_PHI, kx), T(kx)); x2 = Y(Y_DYPHI, kx); }, z, ex, tw, t,
+                 scale, a.phase);
 #pragma unroll
       for (int j = 0; j < J2; ++j)
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) bb[j][k2] = getu(0, j, k2) * z[j][k2].x + getu(1, j, k2) * z[j][k2].y;
       // (dphi/dx3, 0)
-      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZPHI, kx); x2 = zero; }, z, ex, tw, t, scale);
+      xinv<T, N, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZPHI, kx); x2 = zero; }, z, ex, tw, t, scale, a.phase);
 #pragma unroll
       for (int j = 0; j < J2; ++j)
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2)
           z[j][k2] = mk(-aa[j][k2], bb[j][k2] + getu(2, j, k2) * z[j][k2].x);  // (NL3, u.grad phi)
-      xfwd<T, N>(z, store(2), ex, tw, t);
+      xfwd<T, N, KK, SHIFT>(z, store(2), ex, tw, t, a.phase);
     } else {
       // statistics: moments of the diagonal velocity gradients and the scalar
       // gradient (Eqs. 11-12), |omega|^2, u.u, phi u2, phi^2 (Eq. 13)
@@ -743,7 +763,7 @@ k_xpass(PassArgs a) {
         (void)j; (void)k2;
       };
       // (u1, u3)
-      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UZ, kx); }, z, ex, tw, t, scale);
+      xinv<T, N, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UZ, kx); }, z, ex, tw, t, scale, a.phase);
 #pragma unroll
       for (int j = 0; j < J2; ++j)
 #pragma unroll
@@ -753,7 +773,7 @@ k_xpass(PassArgs a) {
           s13[j][k2] = fabs(u1) + fabs(u3);
         }
       // (u2, phi)
-      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UY, kx); x2 = Y(Y_PHI, kx); }, z, ex, tw, t, scale);
+      xinv<T, N, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UY, kx); x2 = Y(Y_PHI, kx); }, z, ex, tw, t, scale, a.phase);
 #pragma unroll
       for (int j = 0; j < J2; ++j)
 #pragma unroll
@@ -765,24 +785,24 @@ k_xpass(PassArgs a) {
           um = max_keep_nan(um, s13[j][k2] + fabs(u2));
         }
       // (omega_1, omega_2)
-      xinv<T, N>(
+      xinv<T, N, KK, SHIFT>(
           [&](int kx, C& x1, C& x2) {
             x1 = Y(Y_WX, kx);
             x2 = csub(Y(Y_DZUX, kx), mul_ik(Y(Y_UZ, kx), T(kx)));
           },
-          z, ex, tw, t, scale);
+          z, ex, tw, t, scale, a.phase);
 #pragma unroll
       for (int j = 0; j < J2; ++j)
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2)
           acc[1].add(z[j][k2].x * z[j][k2].x + z[j][k2].y * z[j][k2].y);
       // (omega_3, dphi/dx1)
-      xinv<T, N>(
+      xinv<T, N, KK, SHIFT>(
           [&](int kx, C& x1, C& x2) {
             x1 = csub(mul_ik(Y(Y_UY, kx), T(kx)), Y(Y_DYUX, kx));
             x2 = mul_ik(Y(Y_PHI, kx), T(kx));
           },
-          z, ex, tw, t, scale);
+          z, ex, tw, t, scale, a.phase);
 #pragma unroll
       for (int j = 0; j < J2; ++j)
 #pragma unroll
@@ -791,8 +811,8 @@ k_xpass(PassArgs a) {
           acc234(11, j, k2, z[j][k2].y);
         }
       // (dphi/dx2, dphi/dx3)
-      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DYPHI, kx); x2 = Y(Y_DZPHI, kx); }, z, ex, tw, t,
-                 scale);
+      xinv<T, N, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DYPHI, kx); x2 = Y(Y_DZPHI, kx); }, z, ex, tw, t,
+                 scale, a.phase);
 #pragma unroll
       for (int j = 0; j < J2; ++j)
 #pragma unroll
@@ -801,8 +821,8 @@ k_xpass(PassArgs a) {
           acc234(17, j, k2, z[j][k2].y);
         }
       // (du1/dx1, du2/dx2)
-      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_UX, kx), T(kx)); x2 = Y(Y_DYUY, kx); }, z,
-                 ex, tw, t, scale);
+      xinv<T, N, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_UX, kx), T(kx)); x2 = Y(Y_DYUY, kx); }, z,
+                 ex, tw, t, scale, a.phase);
 #pragma unroll
       for (int j = 0; j < J2; ++j)
 #pragma unroll
@@ -811,7 +831,7 @@ k_xpass(PassArgs a) {
           acc234(5, j, k2, z[j][k2].y);
         }
       // (du3/dx3, 0)
-      xinv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZUZ, kx); x2 = zero; }, z, ex, tw, t, scale);
+      xinv<T, N, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZUZ, kx); x2 = zero; }, z, ex, tw, t, scale, a.phase);
 #pragma unroll
       for (int j = 0; j < J2; ++j)
 #pragma unroll
@@ -1052,6 +1072,78 @@ template <typename T, int N> struct Passes {
                                  xgrid() * (X2 ? 4 : XCfg<T, N>::WARPS), NV,
                                  {WV0, WV1, 4, 8, 16}, {0, 0, 1, 1, 1},
                                  {MASK_INV, MASK_INV, MASK_FWD, MASK_FWD}};
+    return &tb;
+  }
+};
+
+// Passes of phase-shift dealiasing (section 2.3): the generic strided passes
+// and X pass over the cube |k_i| <= KS that holds the sphere 9|k|^2 < 2 N^2,
+// evaluated on the grid (a.shift = 0) or on the grid shifted by half a cell in
+// every direction (a.shift = 1: inputs times exp(i k pi/N) per axis, outputs
+// times its conjugate).  Grids up to 256 points per side.
+template <typename T, int N> struct PassesPS {
+  static constexpr int KS = sphere_halfwidth(N);
+  static constexpr int TPL = PlanD<N>::TPL;
+  static constexpr int M = KS + 1, P = 2 * KS + 1;
+  static constexpr int WV0 = 8, WV1 = sizeof(T) == 4 ? 16 : 8;
+  static constexpr int NV = WV0 != WV1 ? 2 : 1;
+  static_assert(P <= N, "the sphere's cube must fit the grid");
+  using B = Passes<T, N>;
+
+  template <class KER> static void go(KER k, dim3 grid, dim3 block, size_t sm, const PassArgs& a) {
+    B::prep(k, sm);
+    k<<<grid, block, sm, a.st>>>(a);
+  }
+  template <int W, bool STATS, bool SH> static void zinv_k(const PassArgs& a) {
+    go(k_zinv<T, N, STATS, W, KS, SH>, dim3((M + W - 1) / W, P), dim3(W, TPL), StridedSmem<T, N, W>::BYTES, a);
+  }
+  template <int W, int YM, bool SH> static void yinv_k(const PassArgs& a) {
+    go(k_yinv<T, N, YM, W, KS, SH>, dim3((M + W - 1) / W, N), dim3(W, TPL), StridedSmem<T, N, W>::BYTES, a);
+  }
+  template <int W, bool SH> static void yfwd_k(const PassArgs& a) {
+    go(k_yfwd<T, N, W, KS, SH>, dim3((M + W - 1) / W, N), dim3(W, TPL), StridedSmem<T, N, W>::BYTES, a);
+  }
+  template <int W, bool SH> static void zfwd_k(const PassArgs& a) {
+    go(k_zfwd<T, N, W, KS, SH>, dim3((M + W - 1) / W, P), dim3(W, TPL), StridedSmem<T, N, W>::BYTES, a);
+  }
+  template <int MODE, bool SH> static void xpass_k(const PassArgs& a) {
+    go(k_xpass<T, N, MODE, KS, SH>, dim3(B::xgrid()), dim3(32 * XCfg<T, N>::WARPS), XCfg<T, N>::SMEM, a);
+  }
+  // the 8-stream z-inverse serves the statistics (unshifted) and the
+  // convective form (both grids); the statistics y-inverse and X pass run on
+  // the grid itself only
+  template <int W> static void zinv_w(const PassArgs& a, bool stats) {
+    if (stats) a.shift ? zinv_k<W, true, true>(a) : zinv_k<W, true, false>(a);
+    else a.shift ? zinv_k<W, false, true>(a) : zinv_k<W, false, false>(a);
+  }
+  template <int W> static void yinv_w(const PassArgs& a, int ym) {
+    if (ym == YMODE_STATS) yinv_k<W, YMODE_STATS, false>(a);
+    else if (ym == YMODE_CONVECTIVE) a.shift ? yinv_k<W, YMODE_CONVECTIVE, true>(a) : yinv_k<W, YMODE_CONVECTIVE, false>(a);
+    else a.shift ? yinv_k<W, YMODE_RHS, true>(a) : yinv_k<W, YMODE_RHS, false>(a);
+  }
+  static void zinv(const PassArgs& a, bool stats, int v) { v == 1 ? zinv_w<WV1>(a, stats) : zinv_w<WV0>(a, stats); }
+  static void yinv(const PassArgs& a, int ym, int v) { v == 1 ? yinv_w<WV1>(a, ym) : yinv_w<WV0>(a, ym); }
+  static void yfwd(const PassArgs& a, int v) {
+    if (v == 1) a.shift ? yfwd_k<WV1, true>(a) : yfwd_k<WV1, false>(a);
+    else a.shift ? yfwd_k<WV0, true>(a) : yfwd_k<WV0, false>(a);
+  }
+  static void zfwd(const PassArgs& a, int v) {
+    if (v == 1) a.shift ? zfwd_k<WV1, true>(a) : zfwd_k<WV1, false>(a);
+    else a.shift ? zfwd_k<WV0, true>(a) : zfwd_k<WV0, false>(a);
+  }
+  static void xpass(const PassArgs& a, int mode) {
+    if (mode == XMODE_STATS) return xpass_k<XMODE_STATS, false>(a);
+    if (mode == XMODE_PRESSURE) return a.shift ? xpass_k<XMODE_PRESSURE, true>(a) : xpass_k<XMODE_PRESSURE, false>(a);
+    if (mode == XMODE_CONVECTIVE)
+      return a.shift ? xpass_k<XMODE_CONVECTIVE, true>(a) : xpass_k<XMODE_CONVECTIVE, false>(a);
+    a.shift ? xpass_k<XMODE_RHS, true>(a) : xpass_k<XMODE_RHS, false>(a);
+  }
+  static const PassTable* table() {
+    constexpr unsigned MASK = (1u << NV) - 1u;
+    static const PassTable tb = {&zinv, &yinv, &xpass, &yfwd, &zfwd,
+                                 B::xgrid() * XCfg<T, N>::WARPS, NV,
+                                 {WV0, WV1, WV1, WV1, WV1}, {0, 0, 0, 0, 0},
+                                 {MASK, MASK, MASK, MASK}};
     return &tb;
   }
 };

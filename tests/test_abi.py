@@ -42,8 +42,8 @@ def test_struct_layouts_match_header(lib, tmp_path):
     import shutil
     import subprocess
     from paper_2012_04838_gb300.binding import CParams, CStats
-    # psc_params: 8 int32 + 9 double + 1 uint64 = 112 bytes; psc_stats: 36 doubles + int64
-    assert ct.sizeof(CParams) == 112
+    # psc_params: 10 int32 + 9 double + 1 uint64 = 120 bytes; psc_stats: 36 doubles + int64
+    assert ct.sizeof(CParams) == 120
     assert ct.sizeof(CStats) == 37 * 8
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
