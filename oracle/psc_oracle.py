@@ -673,10 +673,15 @@ def run(p: Params, nsteps: int, uh=None, ph=None, with_records: bool = True):
 def rhs_sparse_triads(modes, N: int, p: Params):
     """N(u, phi) of a state with few non-zero modes, by direct summation.
 
-    ``modes`` maps (kx, ky, kz) with kx >= 0 and |k_i| <= K to
-    (u1, u2, u3, phi) unnormalised coefficients; kx = 0 entries must come in
-    conjugate pairs.  With u(x) = N^-3 sum_p u_p exp(i p.x) (Eq. 5), the
-    products of the retained modes are alias-free on the retained set, so
+    ``modes`` maps retained (kx, ky, kz), kx >= 0, to (u1, u2, u3, phi)
+    unnormalised coefficients; kx = 0 entries must come in conjugate pairs.
+    The retained set is the 2/3 cube |k_i| <= (N-1)//3, or with
+    ``p.dealias`` = DEALIAS_PHASE_SHIFT the sphere 9|k|^2 < 2 N^2 (section
+    2.3).  With u(x) = N^-3 sum_p u_p exp(i p.x) (Eq. 5), the dealiased
+    products of retained modes are alias-free on the retained set (2/3 rule:
+    every alias lands outside the cube; phase shifts: aliases wrapped in one
+    direction cancel between the two grids and the rest land outside the
+    sphere), so
 
         (u x omega)_k   = N^-3 sum_{p+q=k} u_p x (i q x u_q)
         (u.grad phi)_k  = N^-3 sum_{p+q=k} (u_p . i q) phi_q
@@ -684,7 +689,8 @@ def rhs_sparse_triads(modes, N: int, p: Params):
     over the full (conjugate-completed) mode set.  Returns a dict over the
     output modes k (kx >= 0, |k_i| <= K) that receive a contribution or carry
     forcing/source terms: k -> (r1, r2, r3, r_phi) as in rhs_nonlinear."""
-    K = (N - 1) // 3
+    sphere = p.dealias == DEALIAS_PHASE_SHIFT
+    K = sphere_halfwidth(N) if sphere else (N - 1) // 3
     full = {}
     for (kx, ky, kz), v in modes.items():
         v = np.asarray(v, dtype=np.complex128)
@@ -711,7 +717,7 @@ def rhs_sparse_triads(modes, N: int, p: Params):
         for b in range(len(keys)):
             q = kv[b]
             k = pvec + q
-            if k[0] < 0 or np.any(np.abs(k) > K):
+            if k[0] < 0 or np.any(np.abs(k) > K) or (sphere and 9 * int(k @ k) >= 2 * N * N):
                 continue
             uq, phq = vals[b][:3], vals[b][3]
             om = 1j * np.cross(q.astype(np.float64), uq)

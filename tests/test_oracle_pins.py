@@ -555,6 +555,39 @@ def test_sparse_triad_rhs_matches_fft_rhs():
     assert np.abs(np.where(seen[None], 0, ref)).max() < 1e-11 * scale
 
 
+def test_sparse_triad_rhs_matches_fft_rhs_on_the_sphere():
+    # the triad sum restricted to the sphere 9|k|^2 < 2N^2 against the phase-shift
+    # FFT path: modes near the sphere's edge, whose single-grid products alias
+    N = 24
+    K = O.sphere_halfwidth(N)
+    p = O.Params(N=N, nu=0.02, beta=0.9, eps_inj=0.1, kF=2.0, dealias=O.DEALIAS_PHASE_SHIFT)
+    rng = np.random.default_rng(5)
+    modes = {}
+    picks = [(1, 0, 1), (0, 2, -1), (K, 0, 2), (2, K - 1, -3), (6, -6, 5), (0, K, 1), (1, -1, -1)]
+    for k in picks:
+        assert 9 * (k[0] ** 2 + k[1] ** 2 + k[2] ** 2) < 2 * N * N
+        v = rng.standard_normal(4) + 1j * rng.standard_normal(4)
+        modes[k] = v * N ** 3 * 0.1
+        if k[0] == 0:
+            modes[(0, -k[1], -k[2])] = np.conj(modes[k])
+    g = O.Grid(N, O.DEALIAS_PHASE_SHIFT)
+    full = np.zeros((4,) + g.shape_hat, dtype=np.complex128)
+    for (kx, ky, kz), v in modes.items():
+        full[:, kz % N, ky % N, kx] = v
+    ru, rp = O.rhs_nonlinear(full[:3], full[3], g, p)
+    ref = np.array(list(ru) + [rp])
+    got = O.rhs_sparse_triads(modes, N, p)
+    scale = np.abs(ref).max()
+    seen = np.zeros(ref.shape[1:], dtype=bool)
+    for (kx, ky, kz), v in got.items():
+        assert np.abs(ref[:, kz % N, ky % N, kx] - v).max() < 1e-11 * scale
+        seen[kz % N, ky % N, kx] = True
+    assert np.abs(np.where(seen[None], 0, ref)).max() < 1e-11 * scale
+    # some output lies outside the 2/3 cube, where only the sphere keeps it
+    K3 = (N - 1) // 3
+    assert any(max(abs(c) for c in k) > K3 for k in got)
+
+
 # ---------------------------------------------------------------- phase-shift dealiasing
 
 def _sphere_field(g, seed):
