@@ -20,7 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 
-SIZES = (8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 512, 1024)
+SIZES = (8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 512, 520, 1024)
 PRECISIONS = ("float", "double")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -3,14 +3,16 @@
 Each codelet computes X[k] = sum_n x[n] exp(s*2*pi*i*n*k/R) in place on an
 array of R complex values held in registers (s = -1 forward, +1 inverse,
 unnormalised).  Sizes are built by recursive decimation in time from radix-2,
--3 and -4 butterflies; twiddles that are powers of i cost nothing, odd
-multiples of pi/4 cost two multiplies, the rest are complex multiplies by
-literal constants.  Run:  python gen_codelets.py > codelets.cuh
+-3 and -4 butterflies and, for other prime factors p, a direct length-p DFT
+that pairs inputs n and p - n (their sum meets the cosines, their difference
+the sines); twiddles that are powers of i cost nothing, odd multiples of pi/4
+cost two multiplies, the rest are complex multiplies by literal constants.
+Run:  python gen_codelets.py > codelets.cuh
 """
 import math
 import sys
 
-SIZES = (2, 3, 4, 6, 8, 12, 16, 24, 32)
+SIZES = (2, 3, 4, 5, 6, 8, 12, 13, 16, 20, 24, 26, 32)
 
 # Two-step plans N = R1 * R2 of the strided passes (must match Plan<N> in
 # psc_common.cuh).  An inverse pass zero-pads its lines from 2K+1 to N points
@@ -18,7 +20,8 @@ SIZES = (2, 3, 4, 6, 8, 12, 16, 24, 32)
 # for every n2 when R2 n1 > K and R2 n1 + R2 - 1 < N - K: those DFTs are also
 # generated with that input range known to be zero.
 PLANS = {8: (4, 2), 12: (4, 3), 16: (4, 4), 24: (6, 4), 32: (8, 4), 48: (12, 4), 64: (8, 8),
-         96: (12, 8), 128: (16, 8), 192: (24, 8), 256: (16, 16), 512: (32, 16), 1024: (32, 32)}
+         96: (12, 8), 128: (16, 8), 192: (24, 8), 256: (16, 16), 512: (32, 16), 520: (20, 26),
+         1024: (32, 32)}
 
 
 def zero_range(N):
@@ -114,7 +117,9 @@ class Emitter:
             t2 = self.add(b, d)
             t3 = self.rot(self.sub(b, d), s)
             return [self.add(t0, t2), self.add(t1, t3), self.sub(t0, t2), self.sub(t1, t3)]
-        P = 4 if R % 4 == 0 else (2 if R % 2 == 0 else 3)
+        P = 4 if R % 4 == 0 else (2 if R % 2 == 0 else (3 if R % 3 == 0 else smallest_factor(R)))
+        if P == R:
+            return self.prime_dft(xs, s)
         Q = R // P
         Y = {}
         for n2 in range(Q):
@@ -127,6 +132,50 @@ class Emitter:
             for k2 in range(Q):
                 X[k1 + P * k2] = z[k2]
         return X
+
+
+    def lincomb(self, terms):
+        """sum of coef * value over (coef, value) pairs with known-zero values
+        dropped; a string, or None if every value is zero."""
+        parts = [f"{v} * T({c!r})" if c != 1.0 else v for c, v in terms if v is not None]
+        return " + ".join(parts) if parts else None
+
+    def prime_dft(self, xs, s):
+        """Direct DFT of odd prime length R: with a_j = x_j + x_{R-j} and
+        b_j = x_j - x_{R-j} (j = 1 .. (R-1)/2),
+        X_k = x_0 + sum_j cos(2 pi j k/R) a_j + i s sum_j sin(2 pi j k/R) b_j and
+        X_{R-k} the same with the sine sum negated."""
+        R = len(xs)
+        h = (R - 1) // 2
+        a = [None] + [self.add(xs[j], xs[R - j]) for j in range(1, h + 1)]
+        b = [None] + [self.sub(xs[j], xs[R - j]) for j in range(1, h + 1)]
+        X = [None] * R
+        x0 = xs[0]
+        X[0] = x0
+        for j in range(1, h + 1):
+            X[0] = self.add(X[0], a[j])
+        for k in range(1, h + 1):
+            c = [math.cos(2.0 * math.pi * j * k / R) for j in range(h + 1)]
+            sn = [s * math.sin(2.0 * math.pi * j * k / R) for j in range(h + 1)]
+            ar = self.lincomb([(1.0, None if x0 is None else x0[0])] +
+                              [(c[j], None if a[j] is None else a[j][0]) for j in range(1, h + 1)])
+            ai = self.lincomb([(1.0, None if x0 is None else x0[1])] +
+                              [(c[j], None if a[j] is None else a[j][1]) for j in range(1, h + 1)])
+            br = self.lincomb([(sn[j], None if b[j] is None else b[j][0]) for j in range(1, h + 1)])
+            bi = self.lincomb([(sn[j], None if b[j] is None else b[j][1]) for j in range(1, h + 1)])
+            A = None if ar is None else self.new(ar, ai)
+            Bv = None if br is None else self.new(br, bi)
+            iB = self.rot(Bv, 1)
+            X[k] = self.add(A, iB)
+            X[R - k] = self.sub(A, iB)
+        return X
+
+
+def smallest_factor(R):
+    f = 2
+    while R % f:
+        f += 1
+    return f
 
 
 def codelet(R, s, zero=None):

@@ -17,7 +17,7 @@
 // ---------------------------------------------------------------- dispatch
 
 // Grid sizes with compiled pass kernels (one object file per size and precision).
-#define PSC_SIZES(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(512) X(1024)
+#define PSC_SIZES(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(512) X(520) X(1024)
 #define PSC_DECL(n)                                     \
   const psc::PassTable* psc_pass_table_float_##n();     \
   const psc::PassTable* psc_pass_table_double_##n();    \
@@ -170,6 +170,7 @@ struct psc_sim {
   int64_t step;
   int nshell;
   int wv[SP_N];  // tile-width variant of each strided pass (autotuned at creation)
+  int xrow = 0;  // PSC_XPASS_ROWS=1 at creation: the row X pass where the register one exists
   // launch accounting and optional per-launch event timing
   int64_t launches = 0;
   bool profiling = false;
@@ -222,7 +223,11 @@ static psc_status check_params(const psc_params* p) {
   if (p->dealias != PSC_DEALIAS_TWO_THIRDS && p->dealias != PSC_DEALIAS_PHASE_SHIFT)
     return fail(PSC_EINVAL, "bad dealias");
   if (p->dealias == PSC_DEALIAS_PHASE_SHIFT && !table_ps(p->N, p->precision == PSC_FP64))
-    return fail(PSC_EUNSUPPORTED_N, "phase-shift dealiasing is built for N <= 256, not N=" + std::to_string(p->N));
+    return fail(PSC_EUNSUPPORTED_N,
+                "phase-shift dealiasing is built for N <= 256 and N = 520, not N=" + std::to_string(p->N));
+  if (p->nonlinear_form == PSC_NL_CONVECTIVE &&
+      (p->precision == PSC_FP64 ? table_f64(p->N) : table_f32(p->N))->row_only)
+    return fail(PSC_EUNSUPPORTED_N, "the convective form is not built for N=" + std::to_string(p->N));
   if (p->ic < 0 || p->ic > 2) return fail(PSC_EINVAL, "bad ic");
   if (!(p->kF >= 0.0) || !(p->eps_inj >= 0.0)) return fail(PSC_EINVAL, "kF and eps_inj must be >= 0");
   if (!(p->ic_energy >= 0.0) || !(p->ic_noise_frac >= 0.0)) return fail(PSC_EINVAL, "IC energies must be >= 0");
@@ -284,6 +289,11 @@ psc_status psc_create(const psc_params* p, void* dev_ws, size_t ws_bytes, void* 
   sim->ctrl = (Ctrl*)(sim->ws + L.ctrl);
   sim->step = 0;
   sim->nshell = num_shells(sim->d);
+  {
+    // test knob: the shared-memory row X pass at sizes that also have the register one
+    const char* xr = std::getenv("PSC_XPASS_ROWS");
+    sim->xrow = (xr && xr[0] == '1') ? 1 : 0;
+  }
   // twiddles, control block, zero state
   const int N = p->N;
   std::vector<double> twd(2 * (size_t)N);
@@ -417,6 +427,7 @@ PassArgs pass_args(psc_sim* s, const void* in) {
   a.want_umax = 0;
   a.phase = s->ws + s->L.phase;
   a.shift = 0;
+  a.xrow = s->xrow;
   a.st = s->st;
   return a;
 }

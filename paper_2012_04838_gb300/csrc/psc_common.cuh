@@ -69,6 +69,7 @@ PSC_PLAN(128, 16, 8, 8)
 PSC_PLAN(192, 24, 8, 8)
 PSC_PLAN(256, 16, 16, 16)
 PSC_PLAN(512, 32, 16, 16)
+PSC_PLAN(520, 20, 26, 2)
 PSC_PLAN(1024, 32, 32, 32)
 #undef PSC_PLAN
 

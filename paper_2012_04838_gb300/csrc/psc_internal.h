@@ -82,6 +82,7 @@ struct PassArgs {
   int want_umax;    // X pass also reduces max |u1|+|u2|+|u3|
   const void* phase; // exp(i k pi / N), k = -K..K (phase-shift dealiasing)
   int shift;        // 1: evaluate on the grid shifted by half a cell
+  int xrow;         // 1: the shared-memory row X pass where the register one exists
   cudaStream_t st;
 };
 
@@ -106,6 +107,7 @@ struct PassTable {
   int widths[5];    // their column tile widths
   int staged[5];    // 1: input tiles staged through shared memory by TMA
   unsigned vmask[SP_N];  // variants built for each pass (bit v)
+  int row_only;  // 1: the X pass exists only as the row X pass (no convective form)
 };
 
 const PassTable* table_f32(int N);

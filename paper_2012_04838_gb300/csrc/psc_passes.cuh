@@ -116,8 +116,7 @@ __device__ __forceinline__ void strided_fft(const LD& ld, const ST& st,
   using PL = PlanD<N>;
   using SM = StridedSmem<T, N, W>;
   constexpr int R1 = PL::R1, R2 = PL::R2, TPL = PL::TPL, J1 = PL::J1, J2 = PL::J2;
-#pragma unroll
-  for (int j = 0; j < J1; ++j) {
+  auto step1 = [&](int j) {
     const int n2 = t + j * TPL;
     C a[R1];
     static_for<0, R1>([&](auto nc) {
@@ -135,10 +134,8 @@ __device__ __forceinline__ void strided_fft(const LD& ld, const ST& st,
       }
       sm[k1 * SM::ROW + n2 * W + w] = v;
     }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < J2; ++j) {
+  };
+  auto step2 = [&](int j) {
     const int k1 = t + j * TPL;
     C b[R2];
 #pragma unroll
@@ -148,6 +145,22 @@ __device__ __forceinline__ void strided_fft(const LD& ld, const ST& st,
       constexpr int k2 = decltype(kc)::value;
       if constexpr (!(DIR < 0 && dead_k2<N, KK>(k2))) st(k1 + R1 * k2, b[k2]);
     });
+  };
+  // lines split over few lanes (long j loops) stay rolled to bound code size
+  if constexpr (J1 <= 4) {
+#pragma unroll
+    for (int j = 0; j < J1; ++j) step1(j);
+  } else {
+#pragma unroll 1
+    for (int j = 0; j < J1; ++j) step1(j);
+  }
+  __syncthreads();
+  if constexpr (J2 <= 4) {
+#pragma unroll
+    for (int j = 0; j < J2; ++j) step2(j);
+  } else {
+#pragma unroll 1
+    for (int j = 0; j < J2; ++j) step2(j);
   }
   __syncthreads();
 }
@@ -862,6 +875,7 @@ k_xpass(PassArgs a) {
 
 #include "psc_xpass2.cuh"
 #include "psc_staged.cuh"
+#include "psc_xrow.cuh"
 
 namespace psc {
 
@@ -880,6 +894,33 @@ template <typename T, int N> struct Passes {
 #define PSC_X2_MIN_N 512
 #endif
   static constexpr bool X2 = (N == 512 || N == 1024) && N >= PSC_X2_MIN_N;
+  // rows whose plan gives each lane more than 64 values (N = 520: 2 lanes)
+  // take the shared-memory row X pass; it also runs on request (PassArgs::xrow)
+  // at the sizes with the register X pass, for testing
+  static constexpr bool XROW = !X2 && N / TPL > 64;
+  static constexpr bool XROW_OK = !X2;
+  using XRC = XRowCfg<T, N>;
+  static int xrow_grid() {
+    const long long g = ((long long)N * N + XRC::W - 1) / XRC::W;
+    const long long cap = 152 * 64;
+    return (int)(g < cap ? g : cap);
+  }
+  // X-pass CTAs (row X pass) or warps (register X passes) that write statistics partials
+  static int xwarps() {
+    if constexpr (XROW) return xrow_grid();
+    else return xgrid() * (X2 ? 4 : XCfg<T, N>::WARPS);
+  }
+  template <int MODE, int KK, bool SH> static void xrow_k(const PassArgs& a) {
+    if constexpr (XROW_OK) {
+      constexpr int W = XRC::W;
+      // requested at a register-X-pass size: exactly one CTA per partials slot
+      const int grid = XROW ? xrow_grid() : xwarps();
+      prep(k_xrow<T, N, W, MODE, KK, SH>, XRowSmem<T, N, W>::SMEM);
+      k_xrow<T, N, W, MODE, KK, SH><<<grid, dim3(W, TPL), XRowSmem<T, N, W>::SMEM, a.st>>>(a);
+    } else {
+      (void)a;
+    }
+  }
 
   static int xgrid() {
     if constexpr (X2) {
@@ -934,7 +975,7 @@ template <typename T, int N> struct Passes {
 #ifndef PSC_STAGED
 #define PSC_STAGED 1
 #endif
-  static constexpr bool STAGED = PSC_STAGED && sizeof(T) == 4 && N >= 64 && M % 2 == 0;
+  static constexpr bool STAGED = PSC_STAGED && sizeof(T) == 4 && N >= 64 && M % 2 == 0 && TPL >= 4;
   // variant 4: staged, 16 columns, for the inverse passes where it fits one CTA
   static constexpr bool STAGED16 = STAGED && StagedTile<T, N, 16, true>::SMEM <= 227 * 1024;
   static constexpr int NV = STAGED16 ? 5 : STAGED ? 4 : (WV0 != WV1 ? 2 : 1);
@@ -1023,7 +1064,9 @@ template <typename T, int N> struct Passes {
     return n[dev];
   }
   template <int MODE> static void xpass_plain(const PassArgs& a) {
-    if constexpr (X2) {
+    if constexpr (XROW) {
+      (void)a;
+    } else if constexpr (X2) {
       const size_t sm2 = X2Cfg<T, N>::SMEM;
       prep(k_xpass2<T, N, MODE>, sm2);
       k_xpass2<T, N, MODE><<<xgrid(), 128, sm2, a.st>>>(a);
@@ -1033,7 +1076,7 @@ template <typename T, int N> struct Passes {
       k_xpass<T, N, MODE><<<xgrid(), dim3(32 * XCfg<T, N>::WARPS), sm, a.st>>>(a);
     }
   }
-  static void xpass(const PassArgs& a, int mode) {
+  static void xpass_reg(const PassArgs& a, int mode) {
     if (mode == XMODE_PRESSURE) return xpass_plain<XMODE_PRESSURE>(a);
     if (mode == XMODE_CONVECTIVE) return xpass_plain<XMODE_CONVECTIVE>(a);
     if constexpr (X2S) {
@@ -1046,7 +1089,10 @@ template <typename T, int N> struct Passes {
         return;
       }
     }
-    if constexpr (X2) {
+    if constexpr (XROW) {
+      (void)a;
+      (void)mode;
+    } else if constexpr (X2) {
       const size_t sm2 = X2Cfg<T, N>::SMEM;
       if (mode == XMODE_STATS) {
         prep(k_xpass2<T, N, XMODE_STATS>, sm2);
@@ -1067,11 +1113,25 @@ template <typename T, int N> struct Passes {
       }
     }
   }
+  // The row X pass serves the right-hand side, the pressure inputs and the
+  // statistics; the convective form needs the register X passes (it is
+  // refused at the grid sizes that only have the row X pass).
+  static void xpass(const PassArgs& a, int mode) {
+    if constexpr (XROW_OK) {
+      if (XROW || a.xrow) {
+        constexpr int K = PlanD<N>::K;
+        if (mode == XMODE_STATS) return xrow_k<XMODE_STATS, K, false>(a);
+        if (mode == XMODE_PRESSURE) return xrow_k<XMODE_PRESSURE, K, false>(a);
+        if (mode == XMODE_RHS) return xrow_k<XMODE_RHS, K, false>(a);
+      }
+    }
+    if constexpr (!XROW) xpass_reg(a, mode);
+  }
   static const PassTable* table() {
     static const PassTable tb = {&zinv, &yinv, &xpass, &yfwd, &zfwd,
-                                 xgrid() * (X2 ? 4 : XCfg<T, N>::WARPS), NV,
+                                 xwarps(), NV,
                                  {WV0, WV1, 4, 8, 16}, {0, 0, 1, 1, 1},
-                                 {MASK_INV, MASK_INV, MASK_FWD, MASK_FWD}};
+                                 {MASK_INV, MASK_INV, MASK_FWD, MASK_FWD}, XROW ? 1 : 0};
     return &tb;
   }
 };
@@ -1080,7 +1140,7 @@ template <typename T, int N> struct Passes {
 // and X pass over the cube |k_i| <= KS that holds the sphere 9|k|^2 < 2 N^2,
 // evaluated on the grid (a.shift = 0) or on the grid shifted by half a cell in
 // every direction (a.shift = 1: inputs times exp(i k pi/N) per axis, outputs
-// times its conjugate).  Grids up to 256 points per side.
+// times its conjugate).  Grids up to 256 points per side, and 520.
 template <typename T, int N> struct PassesPS {
   static constexpr int KS = sphere_halfwidth(N);
   static constexpr int TPL = PlanD<N>::TPL;
@@ -1107,7 +1167,11 @@ template <typename T, int N> struct PassesPS {
     go(k_zfwd<T, N, W, KS, SH>, dim3((M + W - 1) / W, P), dim3(W, TPL), StridedSmem<T, N, W>::BYTES, a);
   }
   template <int MODE, bool SH> static void xpass_k(const PassArgs& a) {
-    go(k_xpass<T, N, MODE, KS, SH>, dim3(B::xgrid()), dim3(32 * XCfg<T, N>::WARPS), XCfg<T, N>::SMEM, a);
+    if constexpr (B::XROW_OK && MODE != XMODE_CONVECTIVE) {
+      if (B::XROW || a.xrow) return B::template xrow_k<MODE, KS, SH>(a);
+    }
+    if constexpr (!B::XROW)
+      go(k_xpass<T, N, MODE, KS, SH>, dim3(B::xgrid()), dim3(32 * XCfg<T, N>::WARPS), XCfg<T, N>::SMEM, a);
   }
   // the 8-stream z-inverse serves the statistics (unshifted) and the
   // convective form (both grids); the statistics y-inverse and X pass run on
@@ -1141,9 +1205,9 @@ template <typename T, int N> struct PassesPS {
   static const PassTable* table() {
     constexpr unsigned MASK = (1u << NV) - 1u;
     static const PassTable tb = {&zinv, &yinv, &xpass, &yfwd, &zfwd,
-                                 B::xgrid() * XCfg<T, N>::WARPS, NV,
+                                 B::xwarps(), NV,
                                  {WV0, WV1, WV1, WV1, WV1}, {0, 0, 0, 0, 0},
-                                 {MASK, MASK, MASK, MASK}};
+                                 {MASK, MASK, MASK, MASK}, B::XROW ? 1 : 0};
     return &tb;
   }
 };

@@ -60,7 +60,7 @@ def test_struct_layouts_match_header(lib, tmp_path):
 def test_supported_sizes_and_validation(lib):
     from paper_2012_04838_gb300 import binding as B
     sizes = B.supported_sizes()
-    for n in (32, 64, 96, 128, 192, 256, 512, 1024):
+    for n in (32, 64, 96, 128, 192, 256, 512, 520, 1024):
         assert n in sizes
     p = B.Params(N=32)
     assert B.workspace_size(p) > 0

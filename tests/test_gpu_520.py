@@ -1,0 +1,125 @@
+"""The paper's example grid, 520^3 (section 3.1: N = 520 = 2^3 5 13, kF = 2,
+phase shifting and truncation at sqrt(2) N/3), on its own plan (lines of
+20 x 26 points over two lanes, the row X pass).  The oracle cannot transform
+a 520^3 field in a test, so the checks use a sparse state whose right-hand side
+it sums triad by triad, and properties that hold at any size."""
+import numpy as np
+import pytest
+
+from oracle import psc_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+B = pytest.importorskip("paper_2012_04838_gb300.binding")
+
+N = 520
+PS = B.DEALIAS_PHASE_SHIFT
+TWO_THIRDS = B.DEALIAS_TWO_THIRDS
+DNAME = {TWO_THIRDS: "two_thirds", PS: "phase_shift"}
+PNAME = {B.FP64: "fp64", B.FP32_MIXED: "fp32"}
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.load()
+    return torch.device("cuda:0")
+
+
+def _sparse_modes(seed, K, sphere):
+    """Twelve modes from low k to the edge of the retained set, with conjugate
+    partners on kx = 0."""
+    rng = np.random.default_rng(seed)
+    if sphere:
+        e = int(K / np.sqrt(2.0))  # |(e, e, 0)| stays inside the sphere
+        ks = [(1, 0, 1), (0, 2, -1), (2, 1, 0), (1, -1, 2), (3, 2, -2), (K, 0, 1), (0, K - 1, 2),
+              (e, -e, 0), (e - 3, 2, e), (0, 1, 1), (K // 3, K // 2, -K // 2), (2, 0, 0)]
+    else:
+        ks = [(1, 0, 1), (0, 2, -1), (2, 1, 0), (1, -1, 2), (3, 2, -2), (5, -4, 1), (K, -K, 7),
+              (K - 3, K, -K), (K * 3 // 5, -K * 4 // 9, K // 4), (0, 1, 1), (K // 3, K, 0), (2, 0, 0)]
+    modes = {}
+    for k in ks:
+        if sphere:
+            assert 9 * (k[0] ** 2 + k[1] ** 2 + k[2] ** 2) < 2 * N * N
+        v = (rng.standard_normal(4) + 1j * rng.standard_normal(4)) * float(N) ** 3 * 0.05
+        modes[k] = v
+        if k[0] == 0:
+            modes[(0, -k[1], -k[2])] = np.conj(v)
+    return modes
+
+
+@pytest.mark.parametrize("dealias", [TWO_THIRDS, PS], ids=DNAME.get)
+@pytest.mark.parametrize("prec", [B.FP32_MIXED, B.FP64], ids=PNAME.get)
+def test_520_rhs_on_sparse_state_matches_triad_sums(dev, prec, dealias):
+    p = B.Params(N=N, precision=prec, nu=8e-4, beta=1.0, eps_inj=0.1, kF=2.0, dealias=dealias)
+    K = B.retained_halfwidth(N, dealias)
+    modes = _sparse_modes(3 + dealias, K, dealias == PS)
+    cdt = torch.complex64 if prec == B.FP32_MIXED else torch.complex128
+    x = torch.zeros(B.compact_shape(N, dealias), dtype=cdt, device=dev)
+    rounded = {}
+    for (kx, ky, kz), v in modes.items():
+        vv = v.astype(np.complex64) if prec == B.FP32_MIXED else v
+        rounded[(kx, ky, kz)] = vv.astype(np.complex128)
+        x[:, kz + K, ky + K, kx] = torch.from_numpy(vv).to(dev)
+    sim = B.Simulation(p, device=dev)
+    try:
+        out = sim.rhs(x)
+    finally:
+        sim.close()
+    ref = O.rhs_sparse_triads(rounded, N, O.Params(N=N, nu=p.nu, Sc=p.Sc, beta=p.beta, eps_inj=p.eps_inj,
+                                                   kF=p.kF, dealias=dealias))
+    scale = max(np.abs(v).max() for v in ref.values())
+    mask = torch.zeros(B.compact_shape(N, dealias)[1:], dtype=torch.bool, device=dev)
+    got, want = [], []
+    for (kx, ky, kz), v in ref.items():
+        got.append(out[:, kz + K, ky + K, kx].cpu().numpy().astype(np.complex128))
+        want.append(v)
+        mask[kz + K, ky + K, kx] = True
+    got, want = np.array(got), np.array(want)
+    tol = 2e-6 if prec == B.FP32_MIXED else 1e-13
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < tol
+    assert np.abs(got - want).max() < tol * scale
+    # everywhere else only round-off spread by the transforms
+    rest = out.abs().amax(dim=0)
+    rest[mask] = 0
+    assert float(rest.max()) < 5 * tol * scale
+    del out, x
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dealias", [TWO_THIRDS, PS], ids=DNAME.get)
+def test_520_initial_condition_and_records(dev, dealias):
+    """The IC holds the requested energy shell by shell, the grid averages of
+    the statistics X pass agree with the spectral sums, and the paper's
+    deterministic forcing holds the band energy over a few CFL-controlled steps."""
+    p = B.Params(N=N, precision=B.FP32_MIXED, nu=8e-4, Sc=1.0, beta=1.0, kF=2.0, cfl=0.5,
+                 forcing=B.FORCE_HOLD_ENERGY, ic=B.IC_PAPER_EQ9, seed=7, ic_energy=1.5,
+                 record_every=10, dealias=dealias)
+    sim = B.Simulation(p, device=dev)
+    try:
+        sim.init_field()
+        rec, E, Ep = sim.stats()
+        assert len(E) == O.num_shells(N, dealias)
+        assert abs(rec["K"] - 1.5) < 1e-6 * 1.5
+        assert abs(E.sum() - rec["K"]) < 1e-9
+        assert abs(rec["K_phys"] - rec["K"]) < 1e-5 * rec["K"]
+        assert abs(rec["eps_phys"] - rec["eps"]) < 1e-5 * rec["eps"]
+        tgt = O.target_shell_energy(len(E), O.IC_PAPER_EQ9, 1.0, 2.0)
+        live = E > 0
+        assert np.allclose(E[live] / E[live].sum(), tgt[live] / tgt[live].sum(), rtol=1e-5)
+        Ef0 = rec["E_forced"]
+        sim.step(3)
+        rec, E, _ = sim.stats()
+        assert np.isfinite(rec["K"]) and rec["step"] == 3
+        assert abs(rec["E_forced"] - Ef0) < 1e-6 * Ef0
+        assert abs(rec["K_phys"] - rec["K"]) < 1e-5 * rec["K"]
+    finally:
+        sim.close()
+        torch.cuda.empty_cache()
+
+
+def test_520_convective_form_is_refused(dev):
+    with pytest.raises(B.PscError) as e:
+        B.Simulation(B.Params(N=N, precision=B.FP32_MIXED, nonlinear_form=B.NL_CONVECTIVE), device=dev)
+    assert e.value.status == B.PSC_EUNSUPPORTED_N
