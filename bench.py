@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--dealias-compare", action="store_true",
                     help="only time 256^3 steps under the 2/3 rule and under phase-shift dealiasing "
                          "(both precisions) and print steps/s and launches per step")
+    ap.add_argument("--paper-example", action="store_true",
+                    help="only time the paper's example case at 520^3 (phase-shift dealiasing, "
+                         "deterministic forcing, plain RK4, dt = 5e-4) and print steps/s, a per-pass "
+                         "breakdown and a record")
     return ap.parse_args()
 
 
@@ -410,6 +414,51 @@ def run_dealias(N=256, every=10):
     return out
 
 
+def run_paper_example(steps=20):
+    """The example of the paper's section 3 at N = 520: nu = 8e-4, kF = 2, the
+    deterministic forcing that holds the band energy, dt = 5e-4 held fixed,
+    records every 100 steps, IC with the Eq. 9 spectrum at 6 times the energy
+    of u_rms = 1 (K = 9), plain RK4, phase shifting with truncation at
+    sqrt(2) N/3.  Device time of `steps` steps after 3 warm-up steps; one
+    further profiled step gives the per-pass split.  The same case under the
+    2/3 rule, and FP64, for comparison (FP64: 3 steps)."""
+    import torch
+    import paper_2012_04838_gb300 as psc
+    N = 520
+    out = {"N": N, "nu": 8e-4, "dt": 5e-4, "kF": 2.0, "ic_energy": 9.0, "t_end_paper": 40.0}
+    cases = (("fp32_mixed_phase_shift", psc.FP32_MIXED, psc.DEALIAS_PHASE_SHIFT, steps),
+             ("fp32_mixed_two_thirds", psc.FP32_MIXED, psc.DEALIAS_TWO_THIRDS, steps),
+             ("fp64_phase_shift", psc.FP64, psc.DEALIAS_PHASE_SHIFT, 3))
+    for name, prec, dl, n in cases:
+        p = psc.Params(N=N, precision=prec, nu=8e-4, Sc=1.0, beta=1.0, kF=2.0, forcing=psc.FORCE_HOLD_ENERGY,
+                       integrator=psc.INTEG_RK4, dt=5e-4, cfl=0.0, ic=psc.IC_PAPER_EQ9, ic_energy=9.0,
+                       seed=520, record_every=100, dealias=dl)
+        sim = psc.Simulation(p, device="cuda:0")
+        sim.init_field()
+        sim.step(3)
+        st = sim.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st.synchronize()
+        e0.record(st)
+        sim.step(n)
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        sim.profile(True)
+        sim.step(1)
+        split = {k: round(v[0], 3) for k, v in sim.profile_read().items() if v[1]}
+        sim.profile(False)
+        rec, _, _ = sim.stats()
+        out[name] = {"steps_per_s": 1e3 / ms, "ms_per_step": ms, "timed_steps": n,
+                     "workspace_GB": psc.workspace_size(p) / 1e9, "ms_per_kind_one_step": split,
+                     "hours_to_t_end": 40.0 / 5e-4 * ms / 3.6e6,
+                     "record": {k: rec[k] for k in ("step", "t", "K", "eps", "Re_lambda", "kmax_eta_sqrt2",
+                                                    "cfl", "E_forced")}}
+        sim.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_companion(N=512, steps=200, every=10):
     """FP32-mixed against FP64 at 512^3 from the same IC (the 1024^3 workload's
     spectrum, forcing, Sc and CFL 0.5, nu for k_max eta = 1.5): the largest relative
@@ -468,6 +517,9 @@ def main():
         return 0
     if a.dealias_compare:
         print(json.dumps({"dealias_256": run_dealias()}), flush=True)
+        return 0
+    if a.paper_example:
+        print(json.dumps({"paper_example_520": run_paper_example()}), flush=True)
         return 0
 
     import torch

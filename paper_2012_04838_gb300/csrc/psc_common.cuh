@@ -77,6 +77,11 @@ template <int N> struct PlanD : Plan<N> {
   static constexpr int R1 = Plan<N>::R1, R2 = Plan<N>::R2, TPL = Plan<N>::TPL;
   static constexpr int J1 = R2 / TPL, J2 = R1 / TPL;
   static constexpr int K = (N - 1) / 3, M = K + 1, P = 2 * K + 1;
+  // Lines whose lanes would loop more than four times (N = 520 over two lanes)
+  // are transformed "wide" by the strided passes: R2 lanes take the first step
+  // (one length-R1 DFT each), R1 lanes the second.
+  static constexpr bool WIDE = J1 > 4 || J2 > 4;
+  static constexpr int LPL = WIDE ? (R1 > R2 ? R1 : R2) : TPL;  // lanes per line
   static_assert(R1 * R2 == N, "plan must factor N");
   static_assert(R1 % TPL == 0 && R2 % TPL == 0, "TPL must divide both radices");
   static_assert(32 % TPL == 0, "a line's threads must sit inside one warp");

@@ -32,7 +32,7 @@ namespace psc {
 // runs) and the faster is picked per pass and grid size when a simulation is
 // created (see psc_capi.cu); FP64 uses W = 8.
 template <typename T, int N, int W> struct StridedCfg {
-  static constexpr int THREADS = W * PlanD<N>::TPL;
+  static constexpr int THREADS = W * PlanD<N>::LPL;
   // FP32: cap registers at 128 per thread so at least 512 threads fit on an SM;
   // FP64 is bound by the FP64 pipe, so it keeps its values in registers instead
   static constexpr int MINB = sizeof(T) == 8 ? 1 : (THREADS >= 512 ? 1 : 512 / THREADS);
@@ -62,8 +62,12 @@ __device__ __forceinline__ typename CT<T>::type* strided_twiddles(unsigned char*
   C* t = reinterpret_cast<C*>(smraw + StridedSmem<T, N, W>::EXCH_BYTES);
   const int nthr = blockDim.x * blockDim.y, me = threadIdx.y * blockDim.x + threadIdx.x;
   for (int i = me; i < N; i += nthr) {
-    const int tt = i % PL::TPL, k1 = (i / PL::TPL) % PL::R1, j = i / (PL::TPL * PL::R1);
-    t[i] = tw[(tt + j * PL::TPL) * k1];
+    if constexpr (PL::WIDE) {
+      t[i] = tw[i];  // wide lines index wN^(n2 k1) directly
+    } else {
+      const int tt = i % PL::TPL, k1 = (i / PL::TPL) % PL::R1, j = i / (PL::TPL * PL::R1);
+      t[i] = tw[(tt + j * PL::TPL) * k1];
+    }
   }
   __syncthreads();
   return t;
@@ -146,23 +150,39 @@ __device__ __forceinline__ void strided_fft(const LD& ld, const ST& st,
       if constexpr (!(DIR < 0 && dead_k2<N, KK>(k2))) st(k1 + R1 * k2, b[k2]);
     });
   };
-  // lines split over few lanes (long j loops) stay rolled to bound code size
-  if constexpr (J1 <= 4) {
+  if constexpr (PL::WIDE) {
+    // lane t < R2 transforms the R1 points R2 n1 + t; lane t < R1 the R2
+    // points of its k1 = t
+    if (t < R2) {
+      const int n2 = t;
+      C a[R1];
+      static_for<0, R1>([&](auto nc) {
+        constexpr int n1 = decltype(nc)::value;
+        if constexpr (DIR > 0 && ZeroInputs<N, KK>::zero(n1)) a[n1] = mk(T(0), T(0));  // not read
+        else a[n1] = ld(R2 * n1 + n2);
+      });
+      first_dft<T, N, DIR, KK>(a);
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) {
+        C v = a[k1];
+        if (k1 > 0) {
+          const C wv = twsm[n2 * k1];  // wN^(n2 k1), n2 k1 < N
+          v = (DIR < 0) ? cmul(v, wv) : cmulc(v, wv);
+        }
+        sm[k1 * SM::ROW + n2 * W + w] = v;
+      }
+    }
+    __syncthreads();
+    if (t < R1) step2(0);  // k1 = t
+    __syncthreads();
+  } else {
 #pragma unroll
     for (int j = 0; j < J1; ++j) step1(j);
-  } else {
-#pragma unroll 1
-    for (int j = 0; j < J1; ++j) step1(j);
-  }
-  __syncthreads();
-  if constexpr (J2 <= 4) {
+    __syncthreads();
 #pragma unroll
     for (int j = 0; j < J2; ++j) step2(j);
-  } else {
-#pragma unroll 1
-    for (int j = 0; j < J2; ++j) step2(j);
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 // wavenumber of line position p of a zero-padded / truncated axis; false if
@@ -901,7 +921,7 @@ template <typename T, int N> struct Passes {
   static constexpr bool XROW_OK = !X2;
   using XRC = XRowCfg<T, N>;
   static int xrow_grid() {
-    const long long g = ((long long)N * N + XRC::W - 1) / XRC::W;
+    const long long g = ((long long)N * N + XRC::WR - 1) / XRC::WR;
     const long long cap = 152 * 64;
     return (int)(g < cap ? g : cap);
   }
@@ -912,11 +932,12 @@ template <typename T, int N> struct Passes {
   }
   template <int MODE, int KK, bool SH> static void xrow_k(const PassArgs& a) {
     if constexpr (XROW_OK) {
-      constexpr int W = XRC::W;
+      constexpr int WR = XRC::WR;
+      using XS = XRowSmem<T, N, WR>;
       // requested at a register-X-pass size: exactly one CTA per partials slot
       const int grid = XROW ? xrow_grid() : xwarps();
-      prep(k_xrow<T, N, W, MODE, KK, SH>, XRowSmem<T, N, W>::SMEM);
-      k_xrow<T, N, W, MODE, KK, SH><<<grid, dim3(W, TPL), XRowSmem<T, N, W>::SMEM, a.st>>>(a);
+      prep(k_xrow<T, N, WR, MODE, KK, SH>, XS::SMEM);
+      k_xrow<T, N, WR, MODE, KK, SH><<<grid, XS::THREADS, XS::SMEM, a.st>>>(a);
     } else {
       (void)a;
     }
@@ -944,13 +965,13 @@ template <typename T, int N> struct Passes {
 
   template <int W> static void zinv_w(const PassArgs& a, bool stats) {
     constexpr size_t sm = StridedSmem<T, N, W>::BYTES;
-    dim3 grid((M + W - 1) / W, P), block(W, TPL);
+    dim3 grid((M + W - 1) / W, P), block(W, PlanD<N>::LPL);
     if (stats) { prep(k_zinv<T, N, true, W>, sm); k_zinv<T, N, true, W><<<grid, block, sm, a.st>>>(a); }
     else { prep(k_zinv<T, N, false, W>, sm); k_zinv<T, N, false, W><<<grid, block, sm, a.st>>>(a); }
   }
   template <int W, int YM> static void yinv_m(const PassArgs& a) {
     constexpr size_t sm = StridedSmem<T, N, W>::BYTES;
-    dim3 grid((M + W - 1) / W, N), block(W, TPL);
+    dim3 grid((M + W - 1) / W, N), block(W, PlanD<N>::LPL);
     prep(k_yinv<T, N, YM, W>, sm);
     k_yinv<T, N, YM, W><<<grid, block, sm, a.st>>>(a);
   }
@@ -961,13 +982,13 @@ template <typename T, int N> struct Passes {
   }
   template <int W> static void yfwd_w(const PassArgs& a) {
     constexpr size_t sm = StridedSmem<T, N, W>::BYTES;
-    dim3 grid((M + W - 1) / W, N), block(W, TPL);
+    dim3 grid((M + W - 1) / W, N), block(W, PlanD<N>::LPL);
     prep(k_yfwd<T, N, W>, sm);
     k_yfwd<T, N, W><<<grid, block, sm, a.st>>>(a);
   }
   template <int W> static void zfwd_w(const PassArgs& a) {
     constexpr size_t sm = StridedSmem<T, N, W>::BYTES;
-    dim3 grid((M + W - 1) / W, P), block(W, TPL);
+    dim3 grid((M + W - 1) / W, P), block(W, PlanD<N>::LPL);
     prep(k_zfwd<T, N, W>, sm);
     k_zfwd<T, N, W><<<grid, block, sm, a.st>>>(a);
   }
@@ -1155,16 +1176,16 @@ template <typename T, int N> struct PassesPS {
     k<<<grid, block, sm, a.st>>>(a);
   }
   template <int W, bool STATS, bool SH> static void zinv_k(const PassArgs& a) {
-    go(k_zinv<T, N, STATS, W, KS, SH>, dim3((M + W - 1) / W, P), dim3(W, TPL), StridedSmem<T, N, W>::BYTES, a);
+    go(k_zinv<T, N, STATS, W, KS, SH>, dim3((M + W - 1) / W, P), dim3(W, PlanD<N>::LPL), StridedSmem<T, N, W>::BYTES, a);
   }
   template <int W, int YM, bool SH> static void yinv_k(const PassArgs& a) {
-    go(k_yinv<T, N, YM, W, KS, SH>, dim3((M + W - 1) / W, N), dim3(W, TPL), StridedSmem<T, N, W>::BYTES, a);
+    go(k_yinv<T, N, YM, W, KS, SH>, dim3((M + W - 1) / W, N), dim3(W, PlanD<N>::LPL), StridedSmem<T, N, W>::BYTES, a);
   }
   template <int W, bool SH> static void yfwd_k(const PassArgs& a) {
-    go(k_yfwd<T, N, W, KS, SH>, dim3((M + W - 1) / W, N), dim3(W, TPL), StridedSmem<T, N, W>::BYTES, a);
+    go(k_yfwd<T, N, W, KS, SH>, dim3((M + W - 1) / W, N), dim3(W, PlanD<N>::LPL), StridedSmem<T, N, W>::BYTES, a);
   }
   template <int W, bool SH> static void zfwd_k(const PassArgs& a) {
-    go(k_zfwd<T, N, W, KS, SH>, dim3((M + W - 1) / W, P), dim3(W, TPL), StridedSmem<T, N, W>::BYTES, a);
+    go(k_zfwd<T, N, W, KS, SH>, dim3((M + W - 1) / W, P), dim3(W, PlanD<N>::LPL), StridedSmem<T, N, W>::BYTES, a);
   }
   template <int MODE, bool SH> static void xpass_k(const PassArgs& a) {
     if constexpr (B::XROW_OK && MODE != XMODE_CONVECTIVE) {
