@@ -55,8 +55,8 @@ def parse():
                     help="only run 256^3 FP32-mixed and FP64 side by side for 2000 steps and "
                          "print their statistical agreement")
     ap.add_argument("--dealias-compare", action="store_true",
-                    help="only time 256^3 steps under the 2/3 rule and under phase-shift dealiasing "
-                         "(both precisions) and print steps/s and launches per step")
+                    help="only time steps under the 2/3 rule and under phase-shift dealiasing "
+                         "(256^3 both precisions, 1024^3 FP32-mixed) and print steps/s and launches per step")
     ap.add_argument("--paper-example", action="store_true",
                     help="only time the paper's example case at 520^3 (phase-shift dealiasing, "
                          "deterministic forcing, plain RK4, dt = 5e-4) and print steps/s, a per-pass "
@@ -377,16 +377,19 @@ def run_long(N=256, steps=2000, every=10):
     return out
 
 
-def run_dealias(N=256, every=10):
+def run_dealias(every=10):
     """Steps/s of the 2/3 rule and of phase-shift dealiasing (the sphere
     |k| < sqrt(2) N/3, products averaged over the grid and the half-cell-shifted
-    grid) at N^3, FP32-mixed and FP64, CFL 0.5 with a record every 10 steps:
-    device time of the timed steps on the simulation's stream after warm-up."""
+    grid): 256^3 in FP32-mixed and FP64 and 1024^3 in FP32-mixed, CFL 0.5 with
+    a record every 10 steps; device time of the timed steps on the
+    simulation's stream after 3 warm-up steps."""
     import torch
     import paper_2012_04838_gb300 as psc
     from paper_2012_04838_gb300.serve import nu_for_resolution
-    out = {"N": N, "record_every": every}
-    for pname, prec, steps in (("fp32_mixed", psc.FP32_MIXED, 20), ("fp64", psc.FP64, 10)):
+    out = {"record_every": every}
+    for N, pname, prec, steps in ((256, "fp32_mixed", psc.FP32_MIXED, 20), (256, "fp64", psc.FP64, 10),
+                                  (1024, "fp32_mixed", psc.FP32_MIXED, 5)):
+        key = f"N{N}_{pname}"
         for dname, dl in (("two_thirds", psc.DEALIAS_TWO_THIRDS), ("phase_shift", psc.DEALIAS_PHASE_SHIFT)):
             p = psc.Params(N=N, precision=prec, nu=nu_for_resolution(N, 1.5), Sc=1.0, beta=1.0, kF=2.0,
                            eps_inj=0.1, cfl=0.5, ic=psc.IC_SPECTRUM_K4, seed=3, ic_energy=1.5,
@@ -404,13 +407,14 @@ def run_dealias(N=256, every=10):
             e1.synchronize()
             ms = e0.elapsed_time(e1)
             rec, _, _ = sim.stats()
-            out[f"{pname}_{dname}"] = {"steps_per_s": steps / (ms / 1e3), "ms_per_step": ms / steps,
-                                       "steps": steps, "launches_per_step": (sim.launch_count() - n0) / steps,
-                                       "K_end": rec["K"], "eps_end": rec["eps"]}
+            out[f"{key}_{dname}"] = {"steps_per_s": steps / (ms / 1e3), "ms_per_step": ms / steps,
+                                     "steps": steps, "launches_per_step": (sim.launch_count() - n0) / steps,
+                                     "workspace_GB": psc.workspace_size(p) / 1e9,
+                                     "K_end": rec["K"], "eps_end": rec["eps"]}
             sim.close()
             torch.cuda.empty_cache()
-        out[f"{pname}_phase_shift_cost"] = (out[f"{pname}_phase_shift"]["ms_per_step"]
-                                            / out[f"{pname}_two_thirds"]["ms_per_step"])
+        out[f"{key}_phase_shift_cost"] = (out[f"{key}_phase_shift"]["ms_per_step"]
+                                          / out[f"{key}_two_thirds"]["ms_per_step"])
     return out
 
 
@@ -516,7 +520,7 @@ def main():
         print(json.dumps({"companion_512": run_companion()}), flush=True)
         return 0
     if a.dealias_compare:
-        print(json.dumps({"dealias_256": run_dealias()}), flush=True)
+        print(json.dumps({"dealias": run_dealias()}), flush=True)
         return 0
     if a.paper_example:
         print(json.dumps({"paper_example_520": run_paper_example()}), flush=True)

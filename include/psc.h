@@ -63,7 +63,8 @@ typedef enum { PSC_FORCE_NONE = 0, PSC_FORCE_CONST_POWER = 1, PSC_FORCE_HOLD_ENE
 /* Form of the nonlinear term (section 2.3).  ROTATIONAL: P(u x omega), 9
  * physical fields per right-hand side.  CONVECTIVE: -P((u.grad)u) as the paper
  * writes it, with u and the 9 velocity gradients formed in physical space (12
- * fields; a larger workspace).  The two agree to round-off on the retained set. */
+ * fields; a larger workspace).  The two agree to round-off on the retained set.
+ * CONVECTIVE is not built for N = 520 (PSC_EUNSUPPORTED_N). */
 typedef enum { PSC_NL_ROTATIONAL = 0, PSC_NL_CONVECTIVE = 1 } psc_nonlinear;
 typedef enum { PSC_INTEG_IFRK4 = 0, PSC_INTEG_RK4 = 1 } psc_integrator;
 /* Dealiasing of the products (section 2.3).  TWO_THIRDS: the retained set is the
@@ -73,8 +74,9 @@ typedef enum { PSC_INTEG_IFRK4 = 0, PSC_INTEG_RK4 = 1 } psc_integrator;
  * sphere are zero); every product is formed on the grid and on the grid shifted
  * by half a cell in each direction, and the two transforms are averaged, which
  * cancels the aliases that the sphere alone leaves (Patterson and Orszag 1971).
- * Twice the transforms of the right-hand side; built for N <= 256 (else
- * PSC_EUNSUPPORTED_N); psc_pressure is not offered with it (PSC_EINVAL). */
+ * Twice the transforms of the right-hand side.  With it the convective form is
+ * built for N <= 256 only (else PSC_EUNSUPPORTED_N), and psc_pressure is not
+ * offered (PSC_EINVAL). */
 typedef enum { PSC_DEALIAS_TWO_THIRDS = 0, PSC_DEALIAS_PHASE_SHIFT = 1 } psc_dealias;
 
 /* Problem statement (Table 2 of the paper; Sc and beta from section 2.3).

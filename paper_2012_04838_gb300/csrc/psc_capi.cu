@@ -208,6 +208,8 @@ template <class F> void launch(psc_sim* s, int kind, int n, F&& f) {
 
 }  // namespace
 
+static const PassTable* pick_table(const psc_params* p);
+
 static psc_status check_params(const psc_params* p) {
   if (!p) return fail(PSC_EINVAL, "null params");
   if (!size_supported(p->N)) return fail(PSC_EUNSUPPORTED_N, "unsupported grid size N=" + std::to_string(p->N));
@@ -222,12 +224,9 @@ static psc_status check_params(const psc_params* p) {
   if (p->integrator != PSC_INTEG_IFRK4 && p->integrator != PSC_INTEG_RK4) return fail(PSC_EINVAL, "bad integrator");
   if (p->dealias != PSC_DEALIAS_TWO_THIRDS && p->dealias != PSC_DEALIAS_PHASE_SHIFT)
     return fail(PSC_EINVAL, "bad dealias");
-  if (p->dealias == PSC_DEALIAS_PHASE_SHIFT && !table_ps(p->N, p->precision == PSC_FP64))
-    return fail(PSC_EUNSUPPORTED_N,
-                "phase-shift dealiasing is built for N <= 256 and N = 520, not N=" + std::to_string(p->N));
-  if (p->nonlinear_form == PSC_NL_CONVECTIVE &&
-      (p->precision == PSC_FP64 ? table_f64(p->N) : table_f32(p->N))->row_only)
-    return fail(PSC_EUNSUPPORTED_N, "the convective form is not built for N=" + std::to_string(p->N));
+  if (p->nonlinear_form == PSC_NL_CONVECTIVE && pick_table(p)->row_only)
+    return fail(PSC_EUNSUPPORTED_N, std::string("the convective form is not built for N=") + std::to_string(p->N) +
+                                        (p->dealias == PSC_DEALIAS_PHASE_SHIFT ? " with phase-shift dealiasing" : ""));
   if (p->ic < 0 || p->ic > 2) return fail(PSC_EINVAL, "bad ic");
   if (!(p->kF >= 0.0) || !(p->eps_inj >= 0.0)) return fail(PSC_EINVAL, "kF and eps_inj must be >= 0");
   if (!(p->ic_energy >= 0.0) || !(p->ic_noise_frac >= 0.0)) return fail(PSC_EINVAL, "IC energies must be >= 0");

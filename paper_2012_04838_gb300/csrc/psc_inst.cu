@@ -20,11 +20,7 @@ const psc::PassTable* PSC_NAME2(PSC_INST_T, PSC_INST_N)() {
 #define PSC_NAME_PS(t, n) PSC_CAT3(psc_pass_table_ps_, t, _##n)
 #define PSC_NAME_PS2(t, n) PSC_NAME_PS(t, n)
 
-// phase-shift dealiasing: grids up to 256 points per side and 520; null otherwise
+// phase-shift dealiasing
 const psc::PassTable* PSC_NAME_PS2(PSC_INST_T, PSC_INST_N)() {
-#if PSC_INST_N <= 256 || PSC_INST_N == 520
   return psc::PassesPS<PSC_INST_T, PSC_INST_N>::table();
-#else
-  return nullptr;
-#endif
 }

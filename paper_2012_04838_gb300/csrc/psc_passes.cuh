@@ -930,17 +930,18 @@ template <typename T, int N> struct Passes {
     if constexpr (XROW) return xrow_grid();
     else return xgrid() * (X2 ? 4 : XCfg<T, N>::WARPS);
   }
+  // grid: one CTA per statistics partials slot (xwarps()) except where the
+  // row X pass is the only one
+  template <int MODE, int KK, bool SH> static void xrow_launch(const PassArgs& a) {
+    constexpr int WR = XRC::WR;
+    using XS = XRowSmem<T, N, WR>;
+    const int grid = XROW ? xrow_grid() : xwarps();
+    prep(k_xrow<T, N, WR, MODE, KK, SH>, XS::SMEM);
+    k_xrow<T, N, WR, MODE, KK, SH><<<grid, XS::THREADS, XS::SMEM, a.st>>>(a);
+  }
   template <int MODE, int KK, bool SH> static void xrow_k(const PassArgs& a) {
-    if constexpr (XROW_OK) {
-      constexpr int WR = XRC::WR;
-      using XS = XRowSmem<T, N, WR>;
-      // requested at a register-X-pass size: exactly one CTA per partials slot
-      const int grid = XROW ? xrow_grid() : xwarps();
-      prep(k_xrow<T, N, WR, MODE, KK, SH>, XS::SMEM);
-      k_xrow<T, N, WR, MODE, KK, SH><<<grid, XS::THREADS, XS::SMEM, a.st>>>(a);
-    } else {
-      (void)a;
-    }
+    if constexpr (XROW_OK) xrow_launch<MODE, KK, SH>(a);
+    else (void)a;
   }
 
   static int xgrid() {
@@ -1161,7 +1162,7 @@ template <typename T, int N> struct Passes {
 // and X pass over the cube |k_i| <= KS that holds the sphere 9|k|^2 < 2 N^2,
 // evaluated on the grid (a.shift = 0) or on the grid shifted by half a cell in
 // every direction (a.shift = 1: inputs times exp(i k pi/N) per axis, outputs
-// times its conjugate).  Grids up to 256 points per side, and 520.
+// times its conjugate).
 template <typename T, int N> struct PassesPS {
   static constexpr int KS = sphere_halfwidth(N);
   static constexpr int TPL = PlanD<N>::TPL;
@@ -1187,11 +1188,14 @@ template <typename T, int N> struct PassesPS {
   template <int W, bool SH> static void zfwd_k(const PassArgs& a) {
     go(k_zfwd<T, N, W, KS, SH>, dim3((M + W - 1) / W, P), dim3(W, PlanD<N>::LPL), StridedSmem<T, N, W>::BYTES, a);
   }
+  // the sphere's rows at 512, 520 and 1024 go through the row X pass (no
+  // convective form there); smaller grids use the register X pass
+  static constexpr bool ROWS = B::XROW || B::X2;
   template <int MODE, bool SH> static void xpass_k(const PassArgs& a) {
-    if constexpr (B::XROW_OK && MODE != XMODE_CONVECTIVE) {
-      if (B::XROW || a.xrow) return B::template xrow_k<MODE, KS, SH>(a);
+    if constexpr (MODE != XMODE_CONVECTIVE && (ROWS || B::XROW_OK)) {
+      if (ROWS || a.xrow) return B::template xrow_launch<MODE, KS, SH>(a);
     }
-    if constexpr (!B::XROW)
+    if constexpr (!ROWS)
       go(k_xpass<T, N, MODE, KS, SH>, dim3(B::xgrid()), dim3(32 * XCfg<T, N>::WARPS), XCfg<T, N>::SMEM, a);
   }
   // the 8-stream z-inverse serves the statistics (unshifted) and the
@@ -1228,7 +1232,7 @@ template <typename T, int N> struct PassesPS {
     static const PassTable tb = {&zinv, &yinv, &xpass, &yfwd, &zfwd,
                                  B::xwarps(), NV,
                                  {WV0, WV1, WV1, WV1, WV1}, {0, 0, 0, 0, 0},
-                                 {MASK, MASK, MASK, MASK}, B::XROW ? 1 : 0};
+                                 {MASK, MASK, MASK, MASK}, ROWS ? 1 : 0};
     return &tb;
   }
 };

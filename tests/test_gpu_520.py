@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 from oracle import psc_oracle as O
+from tests.sparse_states import check_sparse_rhs
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -27,65 +28,16 @@ def dev():
     return torch.device("cuda:0")
 
 
-def _sparse_modes(seed, K, sphere):
-    """Twelve modes from low k to the edge of the retained set, with conjugate
-    partners on kx = 0."""
-    rng = np.random.default_rng(seed)
-    if sphere:
-        e = int(K / np.sqrt(2.0))  # |(e, e, 0)| stays inside the sphere
-        ks = [(1, 0, 1), (0, 2, -1), (2, 1, 0), (1, -1, 2), (3, 2, -2), (K, 0, 1), (0, K - 1, 2),
-              (e, -e, 0), (e - 3, 2, e), (0, 1, 1), (K // 3, K // 2, -K // 2), (2, 0, 0)]
-    else:
-        ks = [(1, 0, 1), (0, 2, -1), (2, 1, 0), (1, -1, 2), (3, 2, -2), (5, -4, 1), (K, -K, 7),
-              (K - 3, K, -K), (K * 3 // 5, -K * 4 // 9, K // 4), (0, 1, 1), (K // 3, K, 0), (2, 0, 0)]
-    modes = {}
-    for k in ks:
-        if sphere:
-            assert 9 * (k[0] ** 2 + k[1] ** 2 + k[2] ** 2) < 2 * N * N
-        v = (rng.standard_normal(4) + 1j * rng.standard_normal(4)) * float(N) ** 3 * 0.05
-        modes[k] = v
-        if k[0] == 0:
-            modes[(0, -k[1], -k[2])] = np.conj(v)
-    return modes
-
-
 @pytest.mark.parametrize("dealias", [TWO_THIRDS, PS], ids=DNAME.get)
 @pytest.mark.parametrize("prec", [B.FP32_MIXED, B.FP64], ids=PNAME.get)
 def test_520_rhs_on_sparse_state_matches_triad_sums(dev, prec, dealias):
     p = B.Params(N=N, precision=prec, nu=8e-4, beta=1.0, eps_inj=0.1, kF=2.0, dealias=dealias)
-    K = B.retained_halfwidth(N, dealias)
-    modes = _sparse_modes(3 + dealias, K, dealias == PS)
-    cdt = torch.complex64 if prec == B.FP32_MIXED else torch.complex128
-    x = torch.zeros(B.compact_shape(N, dealias), dtype=cdt, device=dev)
-    rounded = {}
-    for (kx, ky, kz), v in modes.items():
-        vv = v.astype(np.complex64) if prec == B.FP32_MIXED else v
-        rounded[(kx, ky, kz)] = vv.astype(np.complex128)
-        x[:, kz + K, ky + K, kx] = torch.from_numpy(vv).to(dev)
     sim = B.Simulation(p, device=dev)
     try:
-        out = sim.rhs(x)
+        check_sparse_rhs(torch, B, sim, 3 + dealias)
     finally:
         sim.close()
-    ref = O.rhs_sparse_triads(rounded, N, O.Params(N=N, nu=p.nu, Sc=p.Sc, beta=p.beta, eps_inj=p.eps_inj,
-                                                   kF=p.kF, dealias=dealias))
-    scale = max(np.abs(v).max() for v in ref.values())
-    mask = torch.zeros(B.compact_shape(N, dealias)[1:], dtype=torch.bool, device=dev)
-    got, want = [], []
-    for (kx, ky, kz), v in ref.items():
-        got.append(out[:, kz + K, ky + K, kx].cpu().numpy().astype(np.complex128))
-        want.append(v)
-        mask[kz + K, ky + K, kx] = True
-    got, want = np.array(got), np.array(want)
-    tol = 2e-6 if prec == B.FP32_MIXED else 1e-13
-    assert np.linalg.norm(got - want) / np.linalg.norm(want) < tol
-    assert np.abs(got - want).max() < tol * scale
-    # everywhere else only round-off spread by the transforms
-    rest = out.abs().amax(dim=0)
-    rest[mask] = 0
-    assert float(rest.max()) < 5 * tol * scale
-    del out, x
-    torch.cuda.empty_cache()
+        torch.cuda.empty_cache()
 
 
 @pytest.mark.parametrize("dealias", [TWO_THIRDS, PS], ids=DNAME.get)

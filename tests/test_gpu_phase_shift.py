@@ -11,6 +11,7 @@ import pytest
 
 from oracle import psc_oracle as O
 from tests.psc_inputs import compact_to_full, full_to_compact, random_compact_state
+from tests.sparse_states import check_sparse_rhs
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -221,7 +222,8 @@ def test_phase_shift_records_match_oracle(dev, prec):
 
 def test_phase_shift_refusals(dev):
     with pytest.raises(B.PscError) as e:
-        B.Simulation(B.Params(N=512, precision=B.FP32_MIXED, dealias=PS), device=dev)
+        B.Simulation(B.Params(N=512, precision=B.FP32_MIXED, dealias=PS, nonlinear_form=B.NL_CONVECTIVE),
+                     device=dev)
     assert e.value.status == B.PSC_EUNSUPPORTED_N
     with pytest.raises(B.PscError) as e:
         B.Simulation(B.Params(N=32, dealias=2), device=dev)
@@ -232,3 +234,22 @@ def test_phase_shift_refusals(dev):
         sim.pressure()
     assert e.value.status == B.PSC_EINVAL
     sim.close()
+
+
+# ---------------------------------------------------------------- full size
+
+@pytest.mark.parametrize("N,prec", [(512, B.FP32_MIXED), (512, B.FP64), (1024, B.FP32_MIXED)],
+                         ids=["512-fp32", "512-fp64", "1024-fp32"])
+def test_phase_shift_full_size_rhs_on_sparse_state_matches_triad_sums(dev, N, prec):
+    """512^3 and 1024^3 (the row X pass over the sphere's cube): a sparse state
+    at the sphere's edge against the oracle's triad sums on the sphere."""
+    p = B.Params(N=N, precision=prec, nu=8e-4, beta=1.0, eps_inj=0.1, kF=2.0, dealias=PS)
+    free, _ = torch.cuda.mem_get_info()
+    if free < B.workspace_size(p) + 16e9:
+        pytest.skip("not enough device memory")
+    sim = B.Simulation(p, device=dev)
+    try:
+        check_sparse_rhs(torch, B, sim, 11 + N)
+    finally:
+        sim.close()
+        torch.cuda.empty_cache()
