@@ -406,9 +406,15 @@ def run_dealias(every=10):
             e1.record(st)
             e1.synchronize()
             ms = e0.elapsed_time(e1)
+            nl = (sim.launch_count() - n0) / steps
+            sim.profile(True)
+            sim.step(1)
+            split = {k: round(v[0], 3) for k, v in sim.profile_read().items() if v[1]}
+            sim.profile(False)
             rec, _, _ = sim.stats()
             out[f"{key}_{dname}"] = {"steps_per_s": steps / (ms / 1e3), "ms_per_step": ms / steps,
-                                     "steps": steps, "launches_per_step": (sim.launch_count() - n0) / steps,
+                                     "steps": steps, "launches_per_step": nl,
+                                     "ms_per_kind_one_step": split,
                                      "workspace_GB": psc.workspace_size(p) / 1e9,
                                      "K_end": rec["K"], "eps_end": rec["eps"]}
             sim.close()

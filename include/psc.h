@@ -74,9 +74,8 @@ typedef enum { PSC_INTEG_IFRK4 = 0, PSC_INTEG_RK4 = 1 } psc_integrator;
  * sphere are zero); every product is formed on the grid and on the grid shifted
  * by half a cell in each direction, and the two transforms are averaged, which
  * cancels the aliases that the sphere alone leaves (Patterson and Orszag 1971).
- * Twice the transforms of the right-hand side.  With it the convective form is
- * built for N <= 256 only (else PSC_EUNSUPPORTED_N), and psc_pressure is not
- * offered (PSC_EINVAL). */
+ * Twice the transforms of the right-hand side; psc_pressure is not offered with
+ * it (PSC_EINVAL). */
 typedef enum { PSC_DEALIAS_TWO_THIRDS = 0, PSC_DEALIAS_PHASE_SHIFT = 1 } psc_dealias;
 
 /* Problem statement (Table 2 of the paper; Sc and beta from section 2.3).

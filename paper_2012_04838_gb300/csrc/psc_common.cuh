@@ -95,14 +95,6 @@ template <int B, int E, class F> __device__ __forceinline__ void static_for(cons
   }
 }
 
-// Positions j + TH m (j < TH) of a length-N line split into 16 slots of TH:
-// 1 if every such position is retained (|k| <= K), 0 if none is, 2 if mixed.
-__host__ __device__ constexpr int band_of(int N, int TH, int m) {
-  return (TH * m + TH - 1 <= (N - 1) / 3 || TH * m >= N - (N - 1) / 3) ? 1
-         : (TH * m > (N - 1) / 3 && TH * m + TH - 1 < N - (N - 1) / 3) ? 0
-                                                                      : 2;
-}
-
 // Per-thread running sum of one statistics moment.  The FP64 path sums in
 // FP64; the FP32 path keeps a compensated FP32 sum (Kahan 1965: the rounding
 // error of each addition is carried into the next), whose error stays within

@@ -1188,15 +1188,19 @@ template <typename T, int N> struct PassesPS {
   template <int W, bool SH> static void zfwd_k(const PassArgs& a) {
     go(k_zfwd<T, N, W, KS, SH>, dim3((M + W - 1) / W, P), dim3(W, PlanD<N>::LPL), StridedSmem<T, N, W>::BYTES, a);
   }
-  // the sphere's rows at 512, 520 and 1024 go through the row X pass (no
-  // convective form there); smaller grids use the register X pass
-  static constexpr bool ROWS = B::XROW || B::X2;
+  // X pass over the sphere's cube: the 16-values-per-thread register pass at
+  // 512 and 1024, the row X pass at 520 (no convective form there), the
+  // generic register pass below
+  static constexpr bool ROWS = B::XROW;
   template <int MODE, bool SH> static void xpass_k(const PassArgs& a) {
     if constexpr (MODE != XMODE_CONVECTIVE && (ROWS || B::XROW_OK)) {
       if (ROWS || a.xrow) return B::template xrow_launch<MODE, KS, SH>(a);
     }
-    if constexpr (!ROWS)
+    if constexpr (B::X2) {
+      go(k_xpass2<T, N, MODE, KS, SH>, dim3(B::xgrid()), dim3(128), X2Cfg<T, N>::SMEM, a);
+    } else if constexpr (!ROWS) {
       go(k_xpass<T, N, MODE, KS, SH>, dim3(B::xgrid()), dim3(32 * XCfg<T, N>::WARPS), XCfg<T, N>::SMEM, a);
+    }
   }
   // the 8-stream z-inverse serves the statistics (unshifted) and the
   // convective form (both grids); the statistics y-inverse and X pass run on

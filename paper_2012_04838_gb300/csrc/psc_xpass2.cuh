@@ -41,6 +41,13 @@ template <typename T, int N> struct X2Cfg {
   static_assert(N == 512 || N == 1024, "X2 layout covers N = 512 and 1024");
 };
 
+// Positions j + TH m (j < TH) of a length-N line split into 16 slots of TH,
+// for the retained half-width K: 1 if every such position is retained, 0 if
+// none is, 2 if mixed.
+__host__ __device__ constexpr int band_of_k(int N, int TH, int m, int K) {
+  return (TH * m + TH - 1 <= K || TH * m >= N - K) ? 1 : (TH * m > K && TH * m + TH - 1 < N - K) ? 0 : 2;
+}
+
 // barrier over the TH threads of one row
 template <int TH> __device__ __forceinline__ void row_sync(int id) {
   if constexpr (TH == 32) {
@@ -103,37 +110,44 @@ template <typename C> struct X2Roles {
 // conj(X1[N-p]) + i conj(X2[N-p]) (p >= N-K), 0 elsewhere.  On return
 // z[b] = scale * IDFT(Z) at n = ra + 16 b + 256 rr (SCALE = false: the
 // unscaled IDFT; the caller folds 1/N^3 into its products).
-template <typename T, int N, bool SCALE = true, class SPEC>
+template <typename T, int N, bool SCALE = true, int KK = (N - 1) / 3, bool SHIFT = false, class SPEC>
 __device__ __forceinline__ void x2inv(const SPEC& spec, typename CT<T>::type (&z)[16],
                                       typename CT<T>::type* ex, const X2Roles<typename CT<T>::type>& q,
-                                      T scale) {
+                                      T scale, const void* phase = nullptr) {
   using C = typename CT<T>::type;
   using XC = X2Cfg<T, N>;
-  constexpr int TH = XC::TH, G = XC::G, ROW = XC::ROW, K = XC::K;
+  constexpr int TH = XC::TH, G = XC::G, ROW = XC::ROW, K = KK;
   C v[16];
   // slots whose positions all lie in the zero band load nothing; slots wholly
   // inside [0, K] or [N-K, N) need no range test
   static_for<0, 16>([&](auto mc) {
     constexpr int m = decltype(mc)::value;
-    constexpr int band = band_of(N, TH, m);
+    constexpr int band = band_of_k(N, TH, m, K);
     constexpr bool low = TH * m <= K;  // slot starts in [0, K]
     const int p = q.tid + TH * m;
     C x1, x2;
+    // the half spectra at k >= 0, times exp(i k pi / N) on the shifted grid
+    auto get = [&](int k) {
+      spec(k, x1, x2);
+      x1 = shift_in<SHIFT, KK>(x1, phase, k);
+      x2 = shift_in<SHIFT, KK>(x2, phase, k);
+    };
     if constexpr (band == 0) {
       v[m] = mk(T(0), T(0));
     } else if constexpr (band == 1 && low) {
-      spec(p, x1, x2);
+      get(p);
       if (m == 0 && p == 0) { x1.y = T(0); x2.y = T(0); }
       v[m] = mk(x1.x - x2.y, x1.y + x2.x);
     } else if constexpr (band == 1) {
-      spec(N - p, x1, x2);
+      get(N - p);
       v[m] = mk(x1.x + x2.y, x2.x - x1.y);
     } else {
       if (p <= K) {
-        spec(p, x1, x2);
+        get(p);
+        if (m == 0 && p == 0) { x1.y = T(0); x2.y = T(0); }
         v[m] = mk(x1.x - x2.y, x1.y + x2.x);
       } else if (p >= N - K) {
-        spec(N - p, x1, x2);
+        get(N - p);
         v[m] = mk(x1.x + x2.y, x2.x - x1.y);
       } else {
         v[m] = mk(T(0), T(0));
@@ -165,12 +179,13 @@ __device__ __forceinline__ void x2inv(const SPEC& spec, typename CT<T>::type (&z
 
 // Forward transform of two real fields packed as x1 + i x2 at the positions
 // x2inv leaves them in; out(kx, X1, X2) receives both half spectra for kx <= K.
-template <typename T, int N, class OUT>
+template <typename T, int N, int KK = (N - 1) / 3, bool SHIFT = false, class OUT>
 __device__ __forceinline__ void x2fwd(typename CT<T>::type (&z)[16], const OUT& out,
-                                      typename CT<T>::type* ex, const X2Roles<typename CT<T>::type>& q) {
+                                      typename CT<T>::type* ex, const X2Roles<typename CT<T>::type>& q,
+                                      const void* phase = nullptr) {
   using C = typename CT<T>::type;
   using XC = X2Cfg<T, N>;
-  constexpr int TH = XC::TH, G = XC::G, ROW = XC::ROW, K = XC::K;
+  constexpr int TH = XC::TH, G = XC::G, ROW = XC::ROW, K = KK;
   lane_dft<T, G, -1>(z, q.rr);  // over c -> k0
   if (q.rk0 > 0) {
 #pragma unroll
@@ -194,14 +209,14 @@ __device__ __forceinline__ void x2fwd(typename CT<T>::type (&z)[16], const OUT& 
   // not computed)
   static_for<0, 16>([&](auto kc) {
     constexpr int k2 = decltype(kc)::value;
-    if constexpr (band_of(N, TH, k2) != 0) ex[q.tid + TH * k2] = v[k2];
+    if constexpr (band_of_k(N, TH, k2, K) != 0) ex[q.tid + TH * k2] = v[k2];
   });
   row_sync<TH>(q.bar);
   for (int kx = q.tid; kx <= K; kx += TH) {
     const C A = ex[kx];
     const C B = ex[kx == 0 ? 0 : N - kx];
-    out(kx, mk(T(0.5) * (A.x + B.x), T(0.5) * (A.y - B.y)),
-        mk(T(0.5) * (A.y + B.y), T(0.5) * (B.x - A.x)));
+    out(kx, shift_out<SHIFT, KK>(mk(T(0.5) * (A.x + B.x), T(0.5) * (A.y - B.y)), phase, kx),
+        shift_out<SHIFT, KK>(mk(T(0.5) * (A.y + B.y), T(0.5) * (B.x - A.x)), phase, kx));
   }
   row_sync<TH>(q.bar);
 }
@@ -233,13 +248,15 @@ __device__ __forceinline__ void x2_twiddles(typename CT<T>::type* t1, const type
 // Y(s, kx) reads stream s at kx.  after_a() runs once streams UX..DYUX are no
 // longer read, wait_b() before PHI..DZPHI are first read (false aborts the
 // row), after_b() once those are no longer read.  Returns false if aborted.
-template <typename T, int N, bool PRESSURE = false, class YF, class HA, class WB, class HB>
+template <typename T, int N, bool PRESSURE = false, int KK = (N - 1) / 3, bool SHIFT = false, class YF, class HA,
+          class WB, class HB>
 __device__ __forceinline__ bool x2_rhs_row(const YF& Y, const HA& after_a, const WB& wait_b, const HB& after_b,
                                            typename CT<T>::type* __restrict__ xb, long long line, long long ys,
                                            typename CT<T>::type* ex, const X2Roles<typename CT<T>::type>& q,
-                                           T scale, bool want_umax, T& um, Ctrl* ctrl) {
+                                           T scale, bool want_umax, T& um, Ctrl* ctrl,
+                                           const void* phase = nullptr) {
   using C = typename CT<T>::type;
-  constexpr int M = X2Cfg<T, N>::K + 1;
+  constexpr int M = KK + 1;
   const C zero = mk(T(0), T(0));
   (void)ctrl;
   C z[16];
@@ -249,11 +266,11 @@ __device__ __forceinline__ bool x2_rhs_row(const YF& Y, const HA& after_a, const
   // live per thread at most: u1, u2, u3 and one more field (64 values)
   T u1[16], u2[16], u3[16], W[16];
   // (u1, u2)
-  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UY, kx); }, z, ex, q, scale);
+  x2inv<T, N, false, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UY, kx); }, z, ex, q, scale, phase);
 #pragma unroll
   for (int b = 0; b < 16; ++b) { u1[b] = z[b].x; u2[b] = z[b].y; }
   // (u3, omega1)
-  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UZ, kx); x2 = Y(Y_WX, kx); }, z, ex, q, scale);
+  x2inv<T, N, false, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UZ, kx); x2 = Y(Y_WX, kx); }, z, ex, q, scale, phase);
 #pragma unroll
   for (int b = 0; b < 16; ++b) {
     u3[b] = z[b].x;
@@ -261,12 +278,12 @@ __device__ __forceinline__ bool x2_rhs_row(const YF& Y, const HA& after_a, const
     if (want_umax) um = max_keep_nan(um, fabs(u1[b]) + fabs(u2[b]) + fabs(u3[b]));
   }
   // (omega2, omega3): omega2 = d_z u1 - i kx u3, omega3 = i kx u2 - d_y u1
-  x2inv<T, N, false>(
+  x2inv<T, N, false, KK, SHIFT>(
       [&](int kx, C& x1, C& x2) {
         x1 = csub(Y(Y_DZUX, kx), mul_ik(Y(Y_UZ, kx), T(kx)));
         x2 = csub(mul_ik(Y(Y_UY, kx), T(kx)), Y(Y_DYUX, kx));
       },
-      z, ex, q, scale);
+      z, ex, q, scale, phase);
   after_a();
 #pragma unroll
   for (int b = 0; b < 16; ++b) {
@@ -274,55 +291,55 @@ __device__ __forceinline__ bool x2_rhs_row(const YF& Y, const HA& after_a, const
     z[b] = mk((u2[b] * w3 - u3[b] * w2) * s2, (u3[b] * w1 - u1[b] * w3) * s2);  // (NL1, NL2)
     W[b] = u1[b] * w2 - u2[b] * w1;                                              // NL3
   }
-  x2fwd<T, N>(z,
+  x2fwd<T, N, KK, SHIFT>(z,
               [&](int kx, C X1, C X2) {
                 const long long i0 = line * M + kx;
                 if (PSC_OK_INDEX(i0 + ys, 4 * ys, ctrl)) { xb[i0] = X1; xb[i0 + ys] = X2; }
               },
-              ex, q);
+              ex, q, phase);
   if constexpr (PRESSURE) {
     // (NL3, |u|^2 / 2): the inputs of the modified pressure
 #pragma unroll
     for (int b = 0; b < 16; ++b)
       z[b] = mk(W[b] * s2, T(0.5) * (u1[b] * u1[b] + u2[b] * u2[b] + u3[b] * u3[b]) * s2);
-    x2fwd<T, N>(z,
+    x2fwd<T, N, KK, SHIFT>(z,
                 [&](int kx, C X1, C X2) {
                   const long long i0 = 2 * ys + line * M + kx;
                   if (PSC_OK_INDEX(i0 + ys, 4 * ys, ctrl)) { xb[i0] = X1; xb[i0 + ys] = X2; }
                 },
-                ex, q);
+                ex, q, phase);
     return true;
   }
   if (!wait_b()) return false;
   // (dphi/dx1, dphi/dx2); u1 then holds the partial u . grad phi
-  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_PHI, kx), T(kx)); x2 = Y(Y_DYPHI, kx); },
-                     z, ex, q, scale);
+  x2inv<T, N, false, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_PHI, kx), T(kx)); x2 = Y(Y_DYPHI, kx); },
+                     z, ex, q, scale, phase);
 #pragma unroll
   for (int b = 0; b < 16; ++b) u1[b] = u1[b] * z[b].x + u2[b] * z[b].y;
   // (dphi/dx3, 0)
-  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZPHI, kx); x2 = zero; }, z, ex, q, scale);
+  x2inv<T, N, false, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZPHI, kx); x2 = zero; }, z, ex, q, scale, phase);
   after_b();
 #pragma unroll
   for (int b = 0; b < 16; ++b) z[b] = mk(W[b] * s2, (u1[b] + u3[b] * z[b].x) * s2);  // (NL3, u.grad phi)
-  x2fwd<T, N>(z,
+  x2fwd<T, N, KK, SHIFT>(z,
               [&](int kx, C X1, C X2) {
                 const long long i0 = 2 * ys + line * M + kx;
                 if (PSC_OK_INDEX(i0 + ys, 4 * ys, ctrl)) { xb[i0] = X1; xb[i0 + ys] = X2; }
               },
-              ex, q);
+              ex, q, phase);
   return true;
 }
 
 // The convective form of one row: -(u.grad)u and u.grad phi from u, its nine
 // gradients and grad phi (8 inverse transforms of packed pairs, 2 forward).
 // With this stream set Y_WX holds d_y u_z and Y_DZUY holds d_z u_y.
-template <typename T, int N, class YF>
+template <typename T, int N, int KK = (N - 1) / 3, bool SHIFT = false, class YF>
 __device__ __forceinline__ void x2_conv_row(const YF& Y, typename CT<T>::type* __restrict__ xb, long long line,
                                             long long ys, typename CT<T>::type* ex,
                                             const X2Roles<typename CT<T>::type>& q, T scale, bool want_umax, T& um,
-                                            Ctrl* ctrl) {
+                                            Ctrl* ctrl, const void* phase = nullptr) {
   using C = typename CT<T>::type;
-  constexpr int M = X2Cfg<T, N>::K + 1;
+  constexpr int M = KK + 1;
   const C zero = mk(T(0), T(0));
   (void)ctrl;
   C z[16];
@@ -335,12 +352,12 @@ __device__ __forceinline__ void x2_conv_row(const YF& Y, typename CT<T>::type* _
     };
   };
   // (u1, u2)
-  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UY, kx); }, z, ex, q, scale);
+  x2inv<T, N, false, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UY, kx); }, z, ex, q, scale, phase);
 #pragma unroll
   for (int b = 0; b < 16; ++b) { u1[b] = z[b].x; u2[b] = z[b].y; }
   // (u3, d1 u1)
-  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UZ, kx); x2 = mul_ik(Y(Y_UX, kx), T(kx)); }, z, ex, q,
-                     scale);
+  x2inv<T, N, false, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UZ, kx); x2 = mul_ik(Y(Y_UX, kx), T(kx)); }, z, ex, q,
+                     scale, phase);
 #pragma unroll
   for (int b = 0; b < 16; ++b) {
     u3[b] = z[b].x;
@@ -348,38 +365,38 @@ __device__ __forceinline__ void x2_conv_row(const YF& Y, typename CT<T>::type* _
     if (want_umax) um = max_keep_nan(um, fabs(u1[b]) + fabs(u2[b]) + fabs(u3[b]));
   }
   // (d2 u1, d3 u1): A = (u.grad) u1
-  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DYUX, kx); x2 = Y(Y_DZUX, kx); }, z, ex, q, scale);
+  x2inv<T, N, false, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DYUX, kx); x2 = Y(Y_DZUX, kx); }, z, ex, q, scale, phase);
 #pragma unroll
   for (int b = 0; b < 16; ++b) A[b] += u2[b] * z[b].x + u3[b] * z[b].y;
   // (d1 u2, d2 u2)
-  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_UY, kx), T(kx)); x2 = Y(Y_DYUY, kx); }, z, ex, q,
-                     scale);
+  x2inv<T, N, false, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_UY, kx), T(kx)); x2 = Y(Y_DYUY, kx); }, z, ex, q,
+                     scale, phase);
 #pragma unroll
   for (int b = 0; b < 16; ++b) B[b] = u1[b] * z[b].x + u2[b] * z[b].y;
   // (d3 u2, d1 u3): B = (u.grad) u2; A starts (u.grad) u3
-  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZUY, kx); x2 = mul_ik(Y(Y_UZ, kx), T(kx)); }, z, ex, q,
-                     scale);
+  x2inv<T, N, false, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZUY, kx); x2 = mul_ik(Y(Y_UZ, kx), T(kx)); }, z, ex, q,
+                     scale, phase);
 #pragma unroll
   for (int b = 0; b < 16; ++b) {
     const T b2 = B[b] + u3[b] * z[b].x, c3 = u1[b] * z[b].y;
     z[b] = mk(-A[b] * s2, -b2 * s2);  // (NL1, NL2)
     A[b] = c3;
   }
-  x2fwd<T, N>(z, out(0), ex, q);
+  x2fwd<T, N, KK, SHIFT>(z, out(0), ex, q, phase);
   // (d2 u3, d3 u3): A = (u.grad) u3
-  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_WX, kx); x2 = Y(Y_DZUZ, kx); }, z, ex, q, scale);
+  x2inv<T, N, false, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_WX, kx); x2 = Y(Y_DZUZ, kx); }, z, ex, q, scale, phase);
 #pragma unroll
   for (int b = 0; b < 16; ++b) A[b] += u2[b] * z[b].x + u3[b] * z[b].y;
   // (dphi/dx1, dphi/dx2)
-  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_PHI, kx), T(kx)); x2 = Y(Y_DYPHI, kx); }, z, ex,
-                     q, scale);
+  x2inv<T, N, false, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_PHI, kx), T(kx)); x2 = Y(Y_DYPHI, kx); }, z, ex,
+                     q, scale, phase);
 #pragma unroll
   for (int b = 0; b < 16; ++b) B[b] = u1[b] * z[b].x + u2[b] * z[b].y;
   // (dphi/dx3, 0)
-  x2inv<T, N, false>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZPHI, kx); x2 = zero; }, z, ex, q, scale);
+  x2inv<T, N, false, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZPHI, kx); x2 = zero; }, z, ex, q, scale, phase);
 #pragma unroll
   for (int b = 0; b < 16; ++b) z[b] = mk(-A[b] * s2, (B[b] + u3[b] * z[b].x) * s2);  // (NL3, u.grad phi)
-  x2fwd<T, N>(z, out(2), ex, q);
+  x2fwd<T, N, KK, SHIFT>(z, out(2), ex, q, phase);
 }
 
 template <typename T>
@@ -389,14 +406,14 @@ __device__ __forceinline__ double warp_sum_d(T v) {
   return d;
 }
 
-template <typename T, int N, int MODE>
 #ifndef PSC_X2_MINB
 #define PSC_X2_MINB 4
 #endif
+template <typename T, int N, int MODE, int KK = (N - 1) / 3, bool SHIFT = false>
 __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : PSC_X2_MINB) k_xpass2(PassArgs a) {
   using C = typename CT<T>::type;
   using XC = X2Cfg<T, N>;
-  constexpr int TH = XC::TH, G = XC::G, ROWS = XC::ROWS, M = XC::K + 1;
+  constexpr int TH = XC::TH, G = XC::G, ROWS = XC::ROWS, M = KK + 1;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int lid = threadIdx.x / TH;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -431,11 +448,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : PSC_X2_MINB) k_xpass
     };
     C z[16];
     if constexpr (MODE == XMODE_RHS || MODE == XMODE_PRESSURE) {
-      x2_rhs_row<T, N, MODE == XMODE_PRESSURE>(Y, [] {}, [] { return true; }, [] {}, xb, line, ys, ex, q, scale,
-                       a.want_umax != 0,
-                       um, a.ctrl);
+      x2_rhs_row<T, N, MODE == XMODE_PRESSURE, KK, SHIFT>(Y, [] {}, [] { return true; }, [] {}, xb, line, ys, ex, q,
+                                                          scale, a.want_umax != 0, um, a.ctrl, a.phase);
     } else if constexpr (MODE == XMODE_CONVECTIVE) {
-      x2_conv_row<T, N>(Y, xb, line, ys, ex, q, scale, a.want_umax != 0, um, a.ctrl);
+      x2_conv_row<T, N, KK, SHIFT>(Y, xb, line, ys, ex, q, scale, a.want_umax != 0, um, a.ctrl, a.phase);
     } else {
       // statistics (Eqs. 11-13): per pair, partial sums of the thread's 16
       // points, added in FP64 to the thread's accumulators (reduced over the
@@ -454,7 +470,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : PSC_X2_MINB) k_xpass
         for (int b = 0; b < 16; ++b) { f1[b] = z[b].x; f2[b] = z[b].y; }
       };
       // (u1, u3)
-      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UZ, kx); }, z, ex, q, scale);
+      x2inv<T, N, true, KK>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UX, kx); x2 = Y(Y_UZ, kx); }, z, ex, q, scale);
       split();
       {
         T s = T(0);
@@ -463,7 +479,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : PSC_X2_MINB) k_xpass
         put(0, s);
       }
       // (u2, phi)
-      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UY, kx); x2 = Y(Y_PHI, kx); }, z, ex, q, scale);
+      x2inv<T, N, true, KK>([&](int kx, C& x1, C& x2) { x1 = Y(Y_UY, kx); x2 = Y(Y_PHI, kx); }, z, ex, q, scale);
       split();
       {
         T s0 = T(0), s1 = T(0), s2 = T(0);
@@ -475,7 +491,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : PSC_X2_MINB) k_xpass
         put(0, s0); put(20, s1); put(21, s2);
       }
       // (omega1, omega2)
-      x2inv<T, N>(
+      x2inv<T, N, true, KK>(
           [&](int kx, C& x1, C& x2) { x1 = Y(Y_WX, kx); x2 = csub(Y(Y_DZUX, kx), mul_ik(Y(Y_UZ, kx), T(kx))); },
           z, ex, q, scale);
       split();
@@ -486,7 +502,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : PSC_X2_MINB) k_xpass
         put(1, s);
       }
       // (omega3, dphi/dx1)
-      x2inv<T, N>(
+      x2inv<T, N, true, KK>(
           [&](int kx, C& x1, C& x2) {
             x1 = csub(mul_ik(Y(Y_UY, kx), T(kx)), Y(Y_DYUX, kx));
             x2 = mul_ik(Y(Y_PHI, kx), T(kx));
@@ -501,18 +517,18 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : PSC_X2_MINB) k_xpass
         mom3(11, f2);
       }
       // (dphi/dx2, dphi/dx3)
-      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DYPHI, kx); x2 = Y(Y_DZPHI, kx); }, z, ex, q, scale);
+      x2inv<T, N, true, KK>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DYPHI, kx); x2 = Y(Y_DZPHI, kx); }, z, ex, q, scale);
       split();
       mom3(14, f1);
       mom3(17, f2);
       // (du1/dx1, du2/dx2)
-      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_UX, kx), T(kx)); x2 = Y(Y_DYUY, kx); }, z, ex,
+      x2inv<T, N, true, KK>([&](int kx, C& x1, C& x2) { x1 = mul_ik(Y(Y_UX, kx), T(kx)); x2 = Y(Y_DYUY, kx); }, z, ex,
                   q, scale);
       split();
       mom3(2, f1);
       mom3(5, f2);
       // (du3/dx3, 0)
-      x2inv<T, N>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZUZ, kx); x2 = zero; }, z, ex, q, scale);
+      x2inv<T, N, true, KK>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZUZ, kx); x2 = zero; }, z, ex, q, scale);
       split();
       mom3(8, f1);
     }

@@ -222,7 +222,7 @@ def test_phase_shift_records_match_oracle(dev, prec):
 
 def test_phase_shift_refusals(dev):
     with pytest.raises(B.PscError) as e:
-        B.Simulation(B.Params(N=512, precision=B.FP32_MIXED, dealias=PS, nonlinear_form=B.NL_CONVECTIVE),
+        B.Simulation(B.Params(N=520, precision=B.FP32_MIXED, dealias=PS, nonlinear_form=B.NL_CONVECTIVE),
                      device=dev)
     assert e.value.status == B.PSC_EUNSUPPORTED_N
     with pytest.raises(B.PscError) as e:
@@ -238,12 +238,14 @@ def test_phase_shift_refusals(dev):
 
 # ---------------------------------------------------------------- full size
 
-@pytest.mark.parametrize("N,prec", [(512, B.FP32_MIXED), (512, B.FP64), (1024, B.FP32_MIXED)],
-                         ids=["512-fp32", "512-fp64", "1024-fp32"])
-def test_phase_shift_full_size_rhs_on_sparse_state_matches_triad_sums(dev, N, prec):
-    """512^3 and 1024^3 (the row X pass over the sphere's cube): a sparse state
-    at the sphere's edge against the oracle's triad sums on the sphere."""
-    p = B.Params(N=N, precision=prec, nu=8e-4, beta=1.0, eps_inj=0.1, kF=2.0, dealias=PS)
+@pytest.mark.parametrize("N,prec,form", [(512, B.FP32_MIXED, B.NL_ROTATIONAL), (512, B.FP64, B.NL_ROTATIONAL),
+                                         (512, B.FP32_MIXED, B.NL_CONVECTIVE), (1024, B.FP32_MIXED, B.NL_ROTATIONAL)],
+                         ids=["512-fp32", "512-fp64", "512-fp32-convective", "1024-fp32"])
+def test_phase_shift_full_size_rhs_on_sparse_state_matches_triad_sums(dev, N, prec, form):
+    """512^3 and 1024^3 (the 16-values-per-thread X pass over the sphere's
+    cube): a sparse state at the sphere's edge against the oracle's triad sums
+    on the sphere (the convective form equals them after projection)."""
+    p = B.Params(N=N, precision=prec, nu=8e-4, beta=1.0, eps_inj=0.1, kF=2.0, dealias=PS, nonlinear_form=form)
     free, _ = torch.cuda.mem_get_info()
     if free < B.workspace_size(p) + 16e9:
         pytest.skip("not enough device memory")
