@@ -358,8 +358,9 @@ def _embed(small, n1, n2):
     return big
 
 
-@pytest.mark.parametrize("N,prec", [(512, B.FP32_MIXED), (512, B.FP64), (1024, B.FP32_MIXED)],
-                         ids=["512-fp32", "512-fp64", "1024-fp32"])
+@pytest.mark.parametrize("N,prec", [(512, B.FP32_MIXED), (512, B.FP64), (520, B.FP32_MIXED), (520, B.FP64),
+                                    (1024, B.FP32_MIXED)],
+                         ids=["512-fp32", "512-fp64", "520-fp32", "520-fp64", "1024-fp32"])
 def test_pressure_of_taylor_green_at_full_size(dev, N, prec):
     """The Taylor-Green field has the closed-form pressure
     (cos 2x + cos 2y)(cos 2z + 2)/16 (pinned in the oracle at 16^3); the same
