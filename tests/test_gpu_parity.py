@@ -303,6 +303,39 @@ def test_state_roundtrip_and_restart_are_bit_exact(dev, prec):
     assert torch.equal(b.get_state().cpu(), end_a)
 
 
+@pytest.mark.parametrize("prec", PREC, ids=PNAME.get)
+def test_state_copies_through_pinned_host_memory_are_bit_exact(dev, prec):
+    """get_state/set_state with pinned host buffers (copied by the SMs through
+    the host mapping), pageable host buffers and device buffers give the same
+    bits, also right after steps and for a buffer offset by 16 bytes."""
+    N = 48
+    p = B.Params(N=N, precision=prec, ic=B.IC_SPECTRUM_K4, seed=8, dt=0.004)
+    a = B.Simulation(p, device=dev)
+    a.init_field()
+    a.step(3)
+    ref = a.get_state()
+    pinned = torch.empty(ref.shape, dtype=ref.dtype, pin_memory=True)
+    nb = a.state_bytes()
+    assert a.lib.psc_get_state(a._h, pinned.data_ptr(), nb) == 0
+    assert torch.equal(pinned, ref.cpu())
+    assert torch.equal(a.get_state(device="cpu"), ref.cpu())
+    # an offset view of a larger pinned block (16-byte aligned, not 256)
+    block = torch.empty(ref.numel() + 2, dtype=ref.dtype, pin_memory=True)
+    view = block[2 // (ref.element_size() // 8):][:ref.numel()].view(ref.shape)
+    assert a.lib.psc_get_state(a._h, view.data_ptr(), nb) == 0
+    assert torch.equal(view, ref.cpu())
+    # set_state from pinned memory, then steps, against set_state from the device
+    b = B.Simulation(p, device=dev)
+    assert b.lib.psc_set_state(b._h, pinned.data_ptr(), nb) == 0
+    b.step(2)
+    c = B.Simulation(p, device=dev)
+    c.set_state(ref)
+    c.step(2)
+    assert torch.equal(b.get_state(), c.get_state())
+    for s in (a, b, c):
+        s.close()
+
+
 def test_unsupported_and_short_workspace(dev):
     with pytest.raises(B.PscError):
         B.Simulation(B.Params(N=100), device=dev)
