@@ -430,10 +430,10 @@ void* device_view(const void* p) {
 
 // State copy between the workspace and a caller buffer on the simulation's
 // stream.  With pinned host memory on the other side the SMs copy through the
-// host mapping: on this platform the copy engines move a state to or from
-// pinned memory at a tenth of that rate right after the solver has run (their
-// address translations of the host pages are cold again), while SM stores and
-// loads keep the link's rate.  Anything else goes through cudaMemcpyAsync.
+// host mapping: on GB300 with a Grace host, the copy engines were measured to
+// move a 1024^3 state to pinned memory at a tenth of the host link's rate right
+// after the solver had run, while SM stores and loads kept the link's rate.
+// Anything else goes through cudaMemcpyAsync.
 cudaError_t copy_state(psc_sim* s, void* dst, const void* src, size_t nb) {
   const bool to_host = src == s->ws + s->L.U;
   void* hv = device_view(to_host ? dst : src);
