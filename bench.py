@@ -61,6 +61,9 @@ def parse():
                     help="only time the paper's example case at 520^3 (phase-shift dealiasing, "
                          "deterministic forcing, plain RK4, dt = 5e-4) and print steps/s, a per-pass "
                          "breakdown and a record")
+    ap.add_argument("--paper-example-steps", type=int, default=0,
+                    help="with --paper-example: also run the FP32-mixed phase-shift case this many steps "
+                         "from its IC, a record every 100 steps (time series of Table 1 and Eqs. 11-12)")
     return ap.parse_args()
 
 
@@ -424,7 +427,7 @@ def run_dealias(every=10):
     return out
 
 
-def run_paper_example(steps=20):
+def run_paper_example(steps=20, run_steps=0):
     """The example of the paper's section 3 at N = 520: nu = 8e-4, kF = 2, the
     deterministic forcing that holds the band energy, dt = 5e-4 held fixed,
     records every 100 steps, IC with the Eq. 9 spectrum at 6 times the energy
@@ -464,6 +467,31 @@ def run_paper_example(steps=20):
                      "hours_to_t_end": 40.0 / 5e-4 * ms / 3.6e6,
                      "record": {k: rec[k] for k in ("step", "t", "K", "eps", "Re_lambda", "kmax_eta_sqrt2",
                                                     "cfl", "E_forced")}}
+        sim.close()
+        torch.cuda.empty_cache()
+    if run_steps > 0:
+        # the development from the IC (the paper's statistics are of the
+        # stationary state after t / T_e ~ 15, which needs 80,000 steps)
+        p = psc.Params(N=N, precision=psc.FP32_MIXED, nu=8e-4, Sc=1.0, beta=1.0, kF=2.0,
+                       forcing=psc.FORCE_HOLD_ENERGY, integrator=psc.INTEG_RK4, dt=5e-4, cfl=0.0,
+                       ic=psc.IC_PAPER_EQ9, ic_energy=9.0, seed=520, record_every=100,
+                       dealias=psc.DEALIAS_PHASE_SHIFT)
+        sim = psc.Simulation(p, device="cuda:0")
+        sim.init_field()
+        series = []
+        t0 = time.perf_counter()
+        for n in range(0, run_steps + 1, 100):
+            if n:
+                sim.step(100)
+            r, _, _ = sim.stats()
+            series.append({"step": r["step"], "t": round(r["t"], 4), "t_over_Te": round(r["t"] / r["Te"], 3),
+                           "K": round(r["K"], 5), "eps": round(r["eps"], 5), "Re_lambda": round(r["Re_lambda"], 2),
+                           "kmax_eta_sqrt2": round(r["kmax_eta_sqrt2"], 4), "cfl": round(r["cfl"], 4),
+                           "skew": [round(v, 4) for v in r["skew"]], "flat": [round(v, 4) for v in r["flat"]],
+                           "skew_phi": [round(v, 4) for v in r["skew_phi"]],
+                           "flat_phi": [round(v, 4) for v in r["flat_phi"]]})
+        out["run_fp32_mixed_phase_shift"] = {"steps": run_steps, "wall_s": time.perf_counter() - t0,
+                                             "records": series}
         sim.close()
         torch.cuda.empty_cache()
     return out
@@ -529,7 +557,7 @@ def main():
         print(json.dumps({"dealias": run_dealias()}), flush=True)
         return 0
     if a.paper_example:
-        print(json.dumps({"paper_example_520": run_paper_example()}), flush=True)
+        print(json.dumps({"paper_example_520": run_paper_example(run_steps=a.paper_example_steps)}), flush=True)
         return 0
 
     import torch
