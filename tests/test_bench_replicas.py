@@ -51,3 +51,16 @@ def test_single_rank_is_unchanged():
     import bench
     assert bench.max_over_ranks(3.5, 1, None) == 3.5
     assert bench.whole_job_rate(10, 1, 500.0) == pytest.approx(20.0)
+
+
+def test_stored_traffic_capture_matches_the_roofline_kernel_sources():
+    """The DRAM traffic that bench.py reports for its roofline kernel comes from
+    a committed capture; its digest must be that of the kernel's current
+    sources (otherwise the bench reports no traffic)."""
+    import json
+    import bench
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with open(os.path.join(root, "profiles", "traffic_xpass_fp32_N1024.json")) as f:
+        tf = json.load(f)
+    assert tf["kernel_digest"] == bench._kernel_digest()
+    assert 0.9 < tf["bytes_per_launch"] / tf["algorithmic_bytes"] < 1.2
