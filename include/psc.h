@@ -155,7 +155,10 @@ psc_status psc_state_bytes(const psc_sim* s, size_t* bytes);
 
 /* Copy the compact state to / from host or device memory (any pointer CUDA can
  * address).  set_state also accepts an initial state from the caller.  Both
- * synchronise the stream. */
+ * synchronise the stream.  Pinned (or registered) host buffers with 16-byte
+ * alignment are copied by the SMs through the host mapping, other buffers by
+ * cudaMemcpyAsync; the bits are the same either way.  `bytes` must equal
+ * psc_state_bytes() (else PSC_EINVAL). */
 psc_status psc_get_state(psc_sim* s, void* dst, size_t bytes);
 psc_status psc_set_state(psc_sim* s, const void* src, size_t bytes);
 
