@@ -40,14 +40,14 @@ def _brute_dft(a):
     return out
 
 
-@pytest.mark.parametrize("N", [8, 12])
+@pytest.mark.parametrize("N", [8, 10, 12, 26])
 def test_fwd_matches_bruteforce_dft(N):
     a = np.random.default_rng(N).standard_normal((N, N, N))
     ref = _brute_dft(a)
     assert np.allclose(O.fwd(a), ref, rtol=0, atol=1e-10 * np.abs(ref).max())
 
 
-@pytest.mark.parametrize("N", [8, 12])
+@pytest.mark.parametrize("N", [8, 10, 12])
 def test_inverse_is_normalised_bruteforce_sum(N):
     g = O.Grid(N)
     _, uh, _ = _rand_velocity(N, 3, solenoidal=False)
@@ -613,7 +613,7 @@ def _exact_product_on_grid(ah, bh, g):
     return out
 
 
-@pytest.mark.parametrize("N", [16, 24])
+@pytest.mark.parametrize("N", [16, 20, 24])
 def test_phase_shift_dealiasing_removes_every_alias(N):
     # Patterson-Orszag: averaging the product formed on the grid and on the grid
     # shifted by half a cell cancels the aliases wrapped an odd number of times;
