@@ -84,3 +84,32 @@ def test_workspace_at_full_size_fits_one_gpu(lib):
     assert 40e9 < w < 80e9
     w = B.workspace_size(B.Params(N=512, precision=B.FP64))
     assert w < 40e9
+
+
+def test_dealiasing_and_form_validation(lib):
+    """Host-side checks of the dealiasing option and of the forms each grid has."""
+    from paper_2012_04838_gb300 import binding as B
+    PS = B.DEALIAS_PHASE_SHIFT
+    for n in (16, 256, 512, 520, 1024):
+        w2 = B.workspace_size(B.Params(N=n, precision=B.FP32_MIXED))
+        wp = B.workspace_size(B.Params(N=n, precision=B.FP32_MIXED, dealias=PS))
+        # the sphere's cube is (sqrt(2) N / 3)^3 / (N / 3)^3 ~ 2.8 times the 2/3 cube's,
+        # plus the products of the unshifted grid
+        assert 1.8 < wp / w2 < 3.6, (n, wp / w2)
+    with pytest.raises(B.PscError) as e:
+        B.workspace_size(B.Params(N=32, dealias=2))
+    assert e.value.status == B.PSC_EINVAL
+    # the convective form exists wherever a register X pass does
+    for n, dl in ((256, PS), (512, PS), (1024, PS), (512, B.DEALIAS_TWO_THIRDS)):
+        assert B.workspace_size(B.Params(N=n, precision=B.FP32_MIXED, dealias=dl,
+                                         nonlinear_form=B.NL_CONVECTIVE)) > 0
+    # ... and not at 520, whose rows only have the shared-memory row X pass
+    for dl in (B.DEALIAS_TWO_THIRDS, PS):
+        with pytest.raises(B.PscError) as e:
+            B.workspace_size(B.Params(N=520, precision=B.FP32_MIXED, dealias=dl,
+                                      nonlinear_form=B.NL_CONVECTIVE))
+        assert e.value.status == B.PSC_EUNSUPPORTED_N
+    # compact shapes follow the retained half-width
+    assert B.compact_shape(520) == (4, 347, 347, 174)
+    assert B.compact_shape(520, PS) == (4, 491, 491, 246)
+    assert B.compact_shape(1024, PS) == (4, 965, 965, 483)
