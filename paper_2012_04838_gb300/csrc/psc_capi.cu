@@ -224,6 +224,7 @@ static psc_status check_params(const psc_params* p) {
   if (p->integrator != PSC_INTEG_IFRK4 && p->integrator != PSC_INTEG_RK4) return fail(PSC_EINVAL, "bad integrator");
   if (p->dealias != PSC_DEALIAS_TWO_THIRDS && p->dealias != PSC_DEALIAS_PHASE_SHIFT)
     return fail(PSC_EINVAL, "bad dealias");
+  if (p->reserved != 0) return fail(PSC_EINVAL, "reserved must be zero");
   if (p->nonlinear_form == PSC_NL_CONVECTIVE && pick_table(p)->row_only)
     return fail(PSC_EUNSUPPORTED_N, std::string("the convective form is not built for N=") + std::to_string(p->N) +
                                         (p->dealias == PSC_DEALIAS_PHASE_SHIFT ? " with phase-shift dealiasing" : ""));

@@ -99,6 +99,11 @@ def test_dealiasing_and_form_validation(lib):
     with pytest.raises(B.PscError) as e:
         B.workspace_size(B.Params(N=32, dealias=2))
     assert e.value.status == B.PSC_EINVAL
+    cp = B.Params(N=32).c()
+    cp.reserved = 1
+    import ctypes as ct
+    n = ct.c_size_t()
+    assert lib.psc_workspace_size(ct.byref(cp), ct.byref(n)) == B.PSC_EINVAL
     # the convective form exists wherever a register X pass does
     for n, dl in ((256, PS), (512, PS), (1024, PS), (512, B.DEALIAS_TWO_THIRDS)):
         assert B.workspace_size(B.Params(N=n, precision=B.FP32_MIXED, dealias=dl,
