@@ -243,25 +243,32 @@ psc_status psc_destroy(psc_sim* s);
  * allocate device memory or provide a workspace (code replayed inside a
  * pre-sized CUDA graph pipeline, plugins whose host application owns the
  * device allocator, tools that only hold a pointer to a state).  It computes
- * the same E(n) and E_phi(n), n = floor(|k| + 1/2), as psc_spectra_and_stats().
+ * the same E(n) and E_phi(n), n = floor(|k| + 1/2), as psc_spectra_and_stats()
+ * of a simulation with the same N, precision and dealias.
  *
  * state: device pointer to a compact state of grid size N in `precision`
- * (layout above).  Ek, Ephi: device pointers to at least nshell_cap doubles;
- * the first nshell(N) entries are written (nshell(1024) = 592).  stream: a
- * cudaStream_t (NULL = default stream); the call is asynchronous on it.
+ * and in the layout `dealias` selects (layout above).  Ek, Ephi: device
+ * pointers to at least nshell_cap doubles; the first nshell entries are
+ * written, nshell = the count psc_spectra_and_stats() reports (2/3 rule:
+ * floor(sqrt(3) K + 1/2) + 1, 592 at N = 1024; phase shifts: K + 2).
+ * stream: a cudaStream_t (NULL = default stream); the call is asynchronous on
+ * it.  PSC_EINVAL, before anything is launched, for: a null pointer; N
+ * outside 8..65536, a bad precision or dealias; nshell_cap < nshell; a state,
+ * Ek or Ephi that is not device (or managed) memory of the current device.
  *
  * The per-shell partial sums go to one fixed device array of
  * PSC_NOALLOC_MAX_SHELLS x 5 doubles inside the library, which every GPU that
  * loads the library holds until the process exits.  Grids needing more shells
- * than that (N >= 1774) are rejected with PSC_EINVAL.  The call allocates no
- * memory.  The first call on each device looks up that array's device address
- * (once per device, with the device current); make that first call before any
- * stream capture.  All calls on a device share the array and it keeps the last
- * call's sums, so calls that overlap on the GPU (different streams, or
- * different host threads) race with each other: serialise them. */
+ * than that (2/3 rule: N >= 1774; phase shifts: N >= 2171) are rejected with
+ * PSC_EINVAL.  The call allocates no memory.  The first call on each device
+ * looks up that array's device address (once per device, with the device
+ * current); make that first call before any stream capture.  All calls on a
+ * device share the array and it keeps the last call's sums, so calls that
+ * overlap on the GPU (different streams, or different host threads) race with
+ * each other: serialise them. */
 #define PSC_NOALLOC_MAX_SHELLS 1024
-psc_status psc_shell_spectra_noalloc(const void* state, int32_t N, int32_t precision, double* Ek,
-                                     double* Ephi, int32_t nshell_cap, void* stream);
+psc_status psc_shell_spectra_noalloc(const void* state, int32_t N, int32_t precision, int32_t dealias,
+                                     double* Ek, double* Ephi, int32_t nshell_cap, void* stream);
 
 /* Message for the last failing call on this thread (never NULL). */
 const char* psc_last_error(void);

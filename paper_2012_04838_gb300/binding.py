@@ -81,7 +81,7 @@ EXPORTS = [
     ("psc_tile_staged", ct.c_int, [_VP, ct.POINTER(ct.c_int32)]),
     ("psc_pressure", ct.c_int, [_VP, _VP, ct.c_size_t]),
     ("psc_destroy", ct.c_int, [_VP]),
-    ("psc_shell_spectra_noalloc", ct.c_int, [_VP, ct.c_int32, ct.c_int32, ct.POINTER(ct.c_double),
+    ("psc_shell_spectra_noalloc", ct.c_int, [_VP, ct.c_int32, ct.c_int32, ct.c_int32, ct.POINTER(ct.c_double),
                                              ct.POINTER(ct.c_double), ct.c_int32, _VP]),
     ("psc_last_error", ct.c_char_p, []),
 ]

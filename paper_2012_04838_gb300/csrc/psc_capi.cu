@@ -92,12 +92,7 @@ static psc_status cuda_fail(cudaError_t e, const char* where) {
 
 // ---------------------------------------------------------------- layout
 
-// Shells n = 0 .. floor(|k|_max + 1/2) of the retained set: the cube's corner
-// |k| = sqrt(3) K, or below sqrt(2) N / 3 for the sphere (at most K + 1).
-static int num_shells(const Dims& d) {
-  if (d.sph) return d.K + 2;
-  return (int)std::floor(std::sqrt(3.0 * d.K * d.K) + 0.5) + 1;
-}
+static int num_shells(const Dims& d) { return shell_count(d); }
 
 struct Layout {
   size_t ctrl, U, V, Acc, zreg, yreg, tw, eu, ep, partials, shells, fac, R0, phase, total;

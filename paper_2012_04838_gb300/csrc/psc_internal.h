@@ -49,6 +49,18 @@ inline Dims make_dims(int N, int sph = 0) {
   return d;
 }
 
+// Shells n = 0 .. floor(|k|_max + 1/2), n = floor(|k| + 1/2), of the retained
+// set: up to the cube's corner |k| = sqrt(3) K under the 2/3 rule; below
+// sqrt(2) N / 3 for the sphere (at most K + 1 there, so K + 2 shells).
+inline int shell_count(const Dims& d) {
+  if (d.sph) return d.K + 2;
+  // largest n with n^2 - n < 3 K^2 (the shell of the corner), in integers
+  const long long k2 = 3LL * d.K * d.K;
+  long long n = 0;
+  while ((n + 1) * (n + 1) - (n + 1) < k2) ++n;
+  return (int)n + 1;
+}
+
 // Device-resident control block: scalars every pass reads or writes.
 struct Ctrl {
   double t, dt;

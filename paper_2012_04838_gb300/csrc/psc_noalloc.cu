@@ -37,11 +37,28 @@ __global__ void k_noalloc_finish(const double* raw, int nshell, double inv2n6, d
   Ephi[n] = raw[nshell + n] * inv2n6;
 }
 
-int shells_for(int N) {
-  const int K = (N - 1) / 3;
-  int n = 0;
-  while ((long long)(n + 1) * (n + 1) - (n + 1) < 3LL * K * K) ++n;  // largest shell holding |k|^2 = 3K^2
-  return n + 1;
+// Whether p is device memory (or managed memory) that device `dev` owns;
+// otherwise `why` says what it is.
+bool on_device(const void* p, int dev, const char* name, std::string& why) {
+  cudaPointerAttributes at;
+  const cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // the failed query leaves a (non-sticky) error: clear it
+    why = std::string(name) + ": not a pointer CUDA knows (" + cudaGetErrorString(e) + ")";
+    return false;
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) {
+    why = std::string(name) + (at.type == cudaMemoryTypeHost ? " is pinned host memory"
+                                                            : " is host memory unknown to CUDA") +
+          ", not device memory";
+    return false;
+  }
+  if (at.type == cudaMemoryTypeDevice && at.device != dev) {
+    why = std::string(name) + " lives on device " + std::to_string(at.device) + ", not on the current device " +
+          std::to_string(dev);
+    return false;
+  }
+  return true;
 }
 
 }  // namespace
@@ -50,17 +67,23 @@ namespace psc {
 void set_error(const std::string& msg);
 }
 
-extern "C" psc_status psc_shell_spectra_noalloc(const void* state, int32_t N, int32_t precision, double* Ek,
-                                                double* Ephi, int32_t nshell_cap, void* stream) {
+extern "C" psc_status psc_shell_spectra_noalloc(const void* state, int32_t N, int32_t precision,
+                                                int32_t dealias, double* Ek, double* Ephi, int32_t nshell_cap,
+                                                void* stream) {
+  // argument checks that need no GPU come first
   if (!state || !Ek || !Ephi) {
     psc::set_error("psc_shell_spectra_noalloc: null pointer");
     return PSC_EINVAL;
   }
-  if (N < 8 || (precision != PSC_FP64 && precision != PSC_FP32_MIXED)) {
-    psc::set_error("psc_shell_spectra_noalloc: N must be >= 8 and precision PSC_FP64 or PSC_FP32_MIXED");
+  if (N < 8 || N > 65536 || (precision != PSC_FP64 && precision != PSC_FP32_MIXED) ||
+      (dealias != PSC_DEALIAS_TWO_THIRDS && dealias != PSC_DEALIAS_PHASE_SHIFT)) {
+    psc::set_error("psc_shell_spectra_noalloc: N must be 8..65536, precision PSC_FP64 or PSC_FP32_MIXED, "
+                   "dealias PSC_DEALIAS_TWO_THIRDS or PSC_DEALIAS_PHASE_SHIFT");
     return PSC_EINVAL;
   }
-  const int nshell = shells_for(N);
+  // the same layout and shell count as a simulation with these parameters
+  const psc::Dims d = psc::make_dims(N, dealias == PSC_DEALIAS_PHASE_SHIFT);
+  const int nshell = psc::shell_count(d);
   if (nshell > kMaxShells) {
     psc::set_error("psc_shell_spectra_noalloc: N=" + std::to_string(N) + " needs " + std::to_string(nshell) +
                    " shells, more than the fixed scratch holds (" + std::to_string(kMaxShells) + ")");
@@ -73,9 +96,21 @@ extern "C" psc_status psc_shell_spectra_noalloc(const void* state, int32_t N, in
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  if (e != cudaSuccess) {
     psc::set_error(std::string("psc_shell_spectra_noalloc: no usable current device: ") + cudaGetErrorString(e));
     return PSC_ECUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    psc::set_error("psc_shell_spectra_noalloc: current device " + std::to_string(dev) + " is beyond the " +
+                   std::to_string(kMaxDevices) + " devices this call keeps scratch addresses for");
+    return PSC_EINVAL;
+  }
+  // a pointer the kernels cannot read on this device is an argument error,
+  // reported before anything is launched
+  std::string why;
+  if (!on_device(state, dev, "state", why) || !on_device(Ek, dev, "Ek", why) || !on_device(Ephi, dev, "Ephi", why)) {
+    psc::set_error("psc_shell_spectra_noalloc: " + why);
+    return PSC_EINVAL;
   }
   double* scratch = nullptr;
   {
@@ -94,17 +129,14 @@ extern "C" psc_status psc_shell_spectra_noalloc(const void* state, int32_t N, in
     }
     scratch = g_scratch_ptr[dev];
   }
-  const psc::Dims d = psc::make_dims(N);
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   // every shell entry the finish kernel reads is rewritten by k_shells first,
   // so nothing left from an earlier call is read
-  if (precision == PSC_FP64) {
-    const unsigned char* u = static_cast<const unsigned char*>(state);
+  const unsigned char* u = static_cast<const unsigned char*>(state);
+  if (precision == PSC_FP64)
     psc::k_shells<double><<<nshell, 256, 0, st>>>(d, u, u + 3 * d.S * 16, nshell, scratch);
-  } else {
-    const unsigned char* u = static_cast<const unsigned char*>(state);
+  else
     psc::k_shells<float><<<nshell, 256, 0, st>>>(d, u, u + 3 * d.S * 8, nshell, scratch);
-  }
   const double n3 = (double)N * N * N;
   k_noalloc_finish<<<(nshell + 127) / 128, 128, 0, st>>>(scratch, nshell, 1.0 / (2.0 * n3 * n3), Ek, Ephi);
   e = cudaGetLastError();

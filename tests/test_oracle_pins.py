@@ -439,6 +439,58 @@ def test_cfl_dt_hits_target():
     assert abs(O.cfl_number(uh, g, dt) - 0.5) < 1e-15
 
 
+@pytest.mark.parametrize("N", [8, 10, 16, 24])
+def test_cfl_maximum_is_of_the_component_sum(N):
+    # Eq. 10 takes max(|u1| + |u2| + |u3|).  For u = a (sin z, sin x, sin y) the
+    # three terms depend on different coordinates, so the maximum of their sum over
+    # the grid is the sum of their maxima, 3 a max_j |sin(2 pi j / N)|: 3a where
+    # the grid holds pi/2 (N divisible by 4).  The largest |u| (sqrt(3) a there)
+    # and the largest component (a) differ from it.
+    a = 1.7
+    x = 2 * np.pi * np.arange(N) / N
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    uh = np.array([O.fwd(a * np.sin(Z)), O.fwd(a * np.sin(X)), O.fwd(a * np.sin(Y))])
+    g = O.Grid(N)
+    want = 3 * a * np.abs(np.sin(x)).max()
+    if N % 4 == 0:
+        assert abs(want - 3 * a) < 1e-15
+    assert abs(O.max_abs_sum(uh, g) - want) < 1e-13
+    dx = 2 * np.pi / N
+    assert abs(O.cfl_number(uh, g, 0.01) - 0.01 / dx * want) < 1e-13
+    assert abs(O.cfl_dt(uh, g, 0.5) - 0.5 * dx / want) < 1e-15
+
+
+def test_skewness_and_flatness_closed_form():
+    # Eqs. 11-12 on fields whose gradients have exact grid moments.  With
+    # u1 = sin x + a sin 2x, u2 = sin y + b sin 2y, u3 = sin z + c sin 2z and
+    # phi = sum of (sin + d sin 2.) over the three axes, each d(.)/dx_i is
+    # f = cos t + e cos 2t (e = 2a, ...), whose grid means are exact for N > 8:
+    #   <f^2> = (1 + e^2)/2,   <f^3> = 3e/4,   <f^4> = 3/8 + 3e^2/2 + 3e^4/8.
+    N = 32
+    x = 2 * np.pi * np.arange(N) / N
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    coef_u = (0.3, -0.7, 0.45)
+    coef_p = (-0.2, 0.6, 1.1)
+    axes = (X, Y, Z)
+    uh = np.array([O.fwd(np.sin(axes[i]) + coef_u[i] * np.sin(2 * axes[i])) for i in range(3)])
+    ph = O.fwd(sum(np.sin(axes[i]) + coef_p[i] * np.sin(2 * axes[i]) for i in range(3)))
+    g = O.Grid(N)
+    s = O.stats(uh, ph, g, O.Params(N=N))
+
+    def closed(c):
+        e = 2 * c
+        m2, m3, m4 = (1 + e * e) / 2, 3 * e / 4, 3 / 8 + 1.5 * e * e + 3 * e ** 4 / 8
+        return m3 / m2 ** 1.5, m4 / m2 ** 2
+
+    for i in range(3):
+        sk, fl = closed(coef_u[i])
+        assert abs(s["skew"][i] - sk) < 1e-12 and abs(s["flat"][i] - fl) < 1e-12
+        sk, fl = closed(coef_p[i])
+        assert abs(s["skew_phi"][i] - sk) < 1e-12 and abs(s["flat_phi"][i] - fl) < 1e-12
+    # the sign follows the third moment: a negative coefficient gives a negative skewness
+    assert s["skew"][1] < 0 < s["skew"][0]
+
+
 # ---------------------------------------------------------------- initial condition
 
 def test_splitmix64_published_vector():
