@@ -741,3 +741,109 @@ def rhs_sparse_triads(modes, N: int, p: Params):
         rp = (-sh - p.beta * v[1]) if p.scalar_on else 0.0
         out[kk] = np.array([nl[0], nl[1], nl[2], rp], dtype=np.complex128)
     return out
+
+
+# --------------------------------------------------------------------------
+# Direct sums for separable states (any N): fields that are sums of products
+# of one-dimensional factors
+# --------------------------------------------------------------------------
+
+class SeparableRHS:
+    """N(u, phi) of Eqs. 7-8 (2/3 rule, rotational form, no linear terms) for a
+    state whose fields are sums of products of 1D factors, at grids too large
+    for the FFT oracle.
+
+    A field f(x) = N^-3 sum_k f_k exp(i k.x) with f_k = sum_t X_t(kx) Y_t(ky)
+    Z_t(kz) is a sum of products a(x1) b(x2) c(x3).  The dealiased product of
+    two such fields keeps, by the definition of the 2/3 rule's alias-free
+    products, (fg)_k = N^-3 sum_{p+q=k} f_p g_q for |k_i| <= K, and for one term
+    of each that sum factorises into three 1D convolutions:
+        (fg)_k = [N^-1 (X * X')(kx)] [N^-1 (Y * Y')(ky)] [N^-1 (Z * Z')(kz)],
+    each restricted to |k| <= K (the cube truncation acts per axis).  Spectral
+    derivatives multiply one factor by i k.  So u x omega and u.grad phi are
+    sums of products of 1D factors, and any plane kz of the output is a small
+    matrix product; projection, forcing and the scalar source are applied on
+    the plane as in ``rhs_nonlinear``.
+
+    ``u_factors`` (3 fields) and ``phi_factors`` are lists of (X, Y, Z) arrays
+    over k = -K..K (index k + K), conjugate-symmetric (real fields)."""
+
+    def __init__(self, u_factors, phi_factors, N: int, p: Params):
+        self.N, self.p = N, p
+        self.K = K = (N - 1) // 3
+        self.k = np.arange(-K, K + 1)
+        u = [[tuple(np.asarray(a, dtype=np.complex128) for a in t) for t in f] for f in u_factors]
+        ph = [tuple(np.asarray(a, dtype=np.complex128) for a in t) for t in phi_factors]
+        self.u = u
+
+        def d(terms, axis):  # derivative along x_{axis+1}: i k on that factor
+            return [tuple(1j * self.k * a if i == axis else a for i, a in enumerate(t)) for t in terms]
+
+        def neg(terms):
+            return [(-t[0], t[1], t[2]) for t in terms]
+
+        # omega = curl u: (d2 u3 - d3 u2, d3 u1 - d1 u3, d1 u2 - d2 u1)
+        w = [d(u[2], 1) + neg(d(u[1], 2)), d(u[0], 2) + neg(d(u[2], 0)), d(u[1], 0) + neg(d(u[0], 1))]
+        self.nl = [self._mul(u[1], w[2]) + neg(self._mul(u[2], w[1])),
+                   self._mul(u[2], w[0]) + neg(self._mul(u[0], w[2])),
+                   self._mul(u[0], w[1]) + neg(self._mul(u[1], w[0]))]
+        self.s = sum((self._mul(u[i], d(ph, i)) for i in range(3)), [])
+        # constant-power forcing amplitude from the band energy (section 2.3)
+        self.A = 0.0
+        if p.forcing == FORCE_CONST_POWER:
+            kb = int(math.floor(p.kF))
+            s_ = 0.0
+            for kz in range(-kb, kb + 1):
+                for ky in range(-kb, kb + 1):
+                    for kx in range(0, kb + 1):
+                        k2 = kx * kx + ky * ky + kz * kz
+                        if 0 < k2 <= p.kF * p.kF and max(kx, abs(ky), abs(kz)) <= K:
+                            w_ = 1.0 if kx == 0 else 2.0
+                            s_ += w_ * sum(abs(self._at(u[c], kx, ky, kz)) ** 2 for c in range(3))
+            ef = s_ / (2.0 * float(N) ** 6)
+            self.A = p.eps_inj / (2.0 * ef) if ef > 1e-300 else 0.0
+
+    def _mul(self, fa, fb):
+        """Terms of the dealiased product of two separable fields."""
+        K, N = self.K, self.N
+        out = []
+        for ta in fa:
+            for tb in fb:
+                out.append(tuple(np.convolve(a, b)[K:3 * K + 1] / N for a, b in zip(ta, tb)))
+        return out
+
+    def _at(self, terms, kx, ky, kz):
+        K = self.K
+        return sum(t[0][kx + K] * t[1][ky + K] * t[2][kz + K] for t in terms)
+
+    def _plane(self, terms, kz):
+        """Dense [ky+K][kx] values (kx >= 0) of a separable field at one kz."""
+        K = self.K
+        X = np.array([t[0][K:] for t in terms])          # (T, K+1)
+        Y = np.array([t[1] for t in terms])              # (T, 2K+1)
+        Z = np.array([t[2][kz + K] for t in terms])      # (T,)
+        return (Y.T * Z) @ X
+
+    def plane(self, kz: int) -> np.ndarray:
+        """The right-hand side (r1, r2, r3, r_phi) at one kz, compact layout
+        [f][ky+K][kx]."""
+        K, p = self.K, self.p
+        kx = np.arange(0, K + 1)[None, :]
+        ky = np.arange(-K, K + 1)[:, None]
+        kzv = float(kz)
+        nl = [self._plane(t, kz) for t in self.nl]
+        k2 = (kx * kx + ky * ky + kz * kz).astype(np.float64)
+        # Leray projection (Eq. 7); k = 0 carries no velocity
+        kd = (kx * nl[0] + ky * nl[1] + kzv * nl[2]) / np.where(k2 == 0, 1.0, k2)
+        nl = [nl[0] - kx * kd, nl[1] - ky * kd, nl[2] - kzv * kd]
+        nl = [np.where(k2 == 0, 0.0, c) for c in nl]
+        u2 = self._plane(self.u[1], kz)
+        bandm = (k2 > 0) & (k2 <= p.kF * p.kF)
+        if p.forcing == FORCE_CONST_POWER:
+            for c in range(3):
+                nl[c] = nl[c] + np.where(bandm, self.A * self._plane(self.u[c], kz), 0.0)
+        if p.scalar_on:
+            rp = -self._plane(self.s, kz) - p.beta * u2
+        else:
+            rp = np.zeros_like(u2)
+        return np.array(nl + [rp])

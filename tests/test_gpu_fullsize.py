@@ -68,11 +68,13 @@ def _sparse_check(s, Nn, prec, seed):
     tol = 2e-6 if prec == B.FP32_MIXED else 1e-13
     assert np.linalg.norm(got - want) / np.linalg.norm(want) < tol
     assert np.abs(got - want).max() < tol * scale
-    # every other mode holds only round-off spread by the transforms: bounded per
-    # element (max over ~10^9 values) at 5x the RHS tolerance of the largest mode
-    rest = out.abs().amax(dim=0)
-    rest[mask] = 0
-    assert float(rest.max()) < 5 * tol * scale
+    # every other mode holds only round-off spread by the transforms: no single
+    # element's error may exceed tol times the norm of the exact output (an
+    # element's error is at most the L2 error of the whole output; the L2 sum
+    # over the ~10^9 zero modes of a sparse state is the dense tests' concern)
+    out[:, mask] = 0
+    rest = float(out.abs().max())
+    assert rest < tol * np.linalg.norm(want), (rest / np.linalg.norm(want), rest / scale)
 
 
 def test_fullsize_rhs_on_sparse_state_matches_triad_sums(sim):

@@ -41,3 +41,37 @@ def test_long_run_statistics_fp32_vs_fp64():
     kmax_half = int((N / 3) / 2)
     rel = np.abs(m32[1:kmax_half + 1] - m64[1:kmax_half + 1]) / m64[1:kmax_half + 1]
     assert rel.max() <= 0.02, rel
+
+
+def _golden_longrun_64():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "longrun_64_oracle.txt")
+    vals = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        parts = line.split()
+        vals[tuple(parts[:-1])] = float(parts[-1])
+    return vals
+
+
+@pytest.mark.parametrize("prec", [B.FP32_MIXED, B.FP64], ids=["fp32", "fp64"])
+def test_long_run_statistics_match_the_oracle_64(prec):
+    """64^3, 2000 forced steps against the FP64 oracle's own run of the same
+    configuration (time averages stored by tests/golden/make_longrun_64.py):
+    E(k) within 2% per shell for k <= k_max/2 and eps within 1%, over all 201
+    records and over the second half."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    N, steps, every = 64, 2000, 10
+    ref = _golden_longrun_64()
+    recs, E = _run(prec, N, steps, every)
+    assert len(recs) == 201
+    kmax_half = int((N / 3) / 2)
+    for tag, rs, Es in (("all", recs, E), ("half", recs[len(recs) // 2:], E[len(recs) // 2:])):
+        eps = np.mean([r["eps"] for r in rs])
+        assert abs(eps - ref[(tag, "eps")]) <= 0.01 * ref[(tag, "eps")], (tag, eps, ref[(tag, "eps")])
+        m = Es.mean(axis=0)
+        want = np.array([ref[(tag, f"E{n}")] for n in range(1, kmax_half + 1)])
+        rel = np.abs(m[1:kmax_half + 1] - want) / want
+        assert rel.max() <= 0.02, (tag, rel)

@@ -8,7 +8,8 @@ import numpy as np
 import pytest
 
 from oracle import psc_oracle as O
-from tests.psc_inputs import compact_to_full, random_compact_state
+from tests.psc_inputs import (compact_to_full, full_to_compact, random_compact_state, separable_compact_state,
+                              separable_factors)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -696,3 +697,25 @@ def test_phase_shift_galerkin_system_conserves_energy_and_forms_agree():
     e = sum(np.sum(g.w * np.real(np.conj(uh[c]) * rot[c])) for c in range(3))
     escale = sum(np.sum(g.w * np.abs(uh[c]) * np.abs(rot[c])) for c in range(3))
     assert abs(e) < 1e-12 * escale
+
+
+# ---------------------------------------------------------------- separable states
+
+@pytest.mark.parametrize("N,forcing,scalar_on", [(24, O.FORCE_CONST_POWER, 1), (32, O.FORCE_NONE, 1),
+                                                 (36, O.FORCE_CONST_POWER, 0)])
+def test_separable_rhs_equals_the_fft_rhs(N, forcing, scalar_on):
+    # the factorised triad sums of SeparableRHS against the FFT right-hand side
+    # of the same (materialised) state, element by element on the retained set
+    f = separable_factors(N, 40 + N, rank=2)
+    c = separable_compact_state(f, N)
+    full = compact_to_full(c, N)
+    p = O.Params(N=N, forcing=forcing, scalar_on=scalar_on, eps_inj=0.1, kF=2.0, beta=0.7)
+    g = O.Grid(N)
+    ru, rp = O.rhs_nonlinear(full[:3], full[3], g, p)
+    want = full_to_compact(np.array(list(ru) + [rp]), N)
+    sep = O.SeparableRHS(f[:3], f[3], N, p)
+    K = (N - 1) // 3
+    got = np.array([sep.plane(kz) for kz in range(-K, K + 1)]).transpose(1, 0, 2, 3)
+    scale = np.abs(want).max()
+    assert scale > 0
+    assert np.abs(got - want).max() < 1e-12 * scale
