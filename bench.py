@@ -61,6 +61,10 @@ def parse():
                     help="only time the paper's example case at 520^3 (phase-shift dealiasing, "
                          "deterministic forcing, plain RK4, dt = 5e-4) and print steps/s, a per-pass "
                          "breakdown and a record")
+    ap.add_argument("--xpass-probe", type=int, default=0, metavar="ROWS",
+                    help="only time the right-hand-side X pass of the --N grid (FP32-mixed) on ROWS rows of "
+                         "synthetic input (psc_xpass_probe; a small footprint for counter captures): "
+                         "--warmup launches, then --steps timed launches")
     ap.add_argument("--paper-example-steps", type=int, default=0,
                     help="with --paper-example: also run the FP32-mixed phase-shift case this many steps "
                          "from its IC, a record every 100 steps (time series of Table 1 and Eqs. 11-12)")
@@ -543,10 +547,37 @@ def run_companion(N=512, steps=200, every=10):
     return out
 
 
+def run_xpass_probe(N, rows, warmup, steps):
+    """CUDA-event time of the X pass on `rows` rows (inputs larger than L2 once
+    rows * 13 streams * (K+1) * 8 B exceeds 129 MB)."""
+    import torch
+
+    import paper_2012_04838_gb300 as psc
+    dev = torch.device("cuda", 0)
+    pr = psc.XPassProbe(N, psc.FP32_MIXED, rows, device=dev)
+    pr.run(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(pr.stream)
+    pr.run(steps)
+    e1.record(pr.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(steps, 1)
+    M = (N - 1) // 3 + 1
+    alg = 13 * rows * M * 8
+    hbm, src = peaks()
+    return {"N": N, "rows": rows, "launches": steps, "ms_per_launch": ms, "algorithmic_bytes": alg,
+            "GBps": alg / ms / 1e6, "frac_of_hbm": alg / ms / 1e6 / hbm, "peak": src,
+            "ms_per_full_pass_scaled": ms * N * N / rows, "buffer_GB": pr.nbytes / 1e9}
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.xpass_probe:
+        print(json.dumps({"xpass_probe": run_xpass_probe(a.N, a.xpass_probe, a.warmup, a.steps)}), flush=True)
+        return 0
     if a.long_run:
         print(json.dumps({"long_run": run_long()}), flush=True)
         return 0
@@ -631,16 +662,7 @@ def main():
                       "GBps": round(kb[k] / (v[0] / v[1] / 1000.0) / 1e9, 1) if (v[1] and k in kb) else None}
                   for k, v in prof.items()}
     step_bytes = 4 * sum(kb.values())
-    traffic = None
-    prof_file = os.path.join(ROOT, "profiles", f"traffic_{dom}_fp32_N{N}.json")
-    if os.path.exists(prof_file):
-        try:
-            with open(prof_file) as f:
-                tf = json.load(f)
-            if tf.get("kernel_digest") == _kernel_digest():
-                traffic = tf.get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = stored_traffic(dom, N)
 
     out = {"metric": "RK4 steps/s", "value": value, "unit": "steps/s", "n_gpus": world,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
@@ -749,6 +771,19 @@ def main():
 
 # the sources the roofline kernel (the 1024^3 FP32 x pass, k_xpass2s) is built from
 DOMINANT_KERNEL_SOURCES = ("psc_xpass2.cuh", "psc_common.cuh", "psc_internal.h", "codelets.cuh")
+
+
+def stored_traffic(kind: str, N: int):
+    """DRAM bytes per launch of kernel `kind` from the committed capture
+    profiles/traffic_<kind>_fp32_N<N>.json, or None when there is none or it was
+    taken of other kernel sources than the current ones."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{kind}_fp32_N{N}.json")
+    try:
+        with open(path) as f:
+            tf = json.load(f)
+    except Exception:
+        return None
+    return tf.get("bytes_per_launch") if tf.get("kernel_digest") == _kernel_digest() else None
 
 
 def _kernel_digest() -> str:

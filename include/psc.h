@@ -270,6 +270,20 @@ psc_status psc_destroy(psc_sim* s);
 psc_status psc_shell_spectra_noalloc(const void* state, int32_t N, int32_t precision, int32_t dealias,
                                      double* Ek, double* Ephi, int32_t nshell_cap, void* stream);
 
+/* Profiling aid (no counterpart in the paper): the right-hand-side X pass
+ * that psc_step() runs for grid size N and precision (2/3 rule), launched
+ * nlaunch times over `rows` rows of a deterministic synthetic input instead of
+ * the N*N rows of a box, so that hardware-counter captures of it fit in a few
+ * GB of device memory.  rows: a positive multiple of 64, at most N*N.  buf:
+ * caller-owned device memory of psc_xpass_probe_bytes() bytes, 256-byte
+ * aligned, holding a control block, twiddles, the nine input streams
+ * [stream][row][kx] and the four output streams; the call fills all but the
+ * outputs.  Asynchronous on `stream`.  N = 520 (row X pass only) is refused
+ * with PSC_EUNSUPPORTED_N. */
+psc_status psc_xpass_probe_bytes(int32_t N, int32_t precision, int64_t rows, size_t* bytes);
+psc_status psc_xpass_probe(int32_t N, int32_t precision, int64_t rows, void* buf, size_t bytes, void* stream,
+                           int32_t nlaunch);
+
 /* Message for the last failing call on this thread (never NULL). */
 const char* psc_last_error(void);
 

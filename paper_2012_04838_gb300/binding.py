@@ -83,6 +83,8 @@ EXPORTS = [
     ("psc_destroy", ct.c_int, [_VP]),
     ("psc_shell_spectra_noalloc", ct.c_int, [_VP, ct.c_int32, ct.c_int32, ct.c_int32, ct.POINTER(ct.c_double),
                                              ct.POINTER(ct.c_double), ct.c_int32, _VP]),
+    ("psc_xpass_probe_bytes", ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int64, ct.POINTER(_SZ)]),
+    ("psc_xpass_probe", ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int64, _VP, _SZ, _VP, ct.c_int32]),
     ("psc_last_error", ct.c_char_p, []),
 ]
 
@@ -349,3 +351,25 @@ class Batch:
         except Exception:
             pass
 
+
+
+class XPassProbe:
+    """The right-hand-side X pass of an N-grid over `rows` rows of synthetic
+    input (psc_xpass_probe): a small-footprint stand-in for profiling."""
+
+    def __init__(self, N: int, precision: int, rows: int, device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.lib = load()
+        self.N, self.precision, self.rows = N, precision, rows
+        self.device = torch.device(device if device is not None else "cuda")
+        n = ct.c_size_t()
+        _check(self.lib, self.lib.psc_xpass_probe_bytes(N, precision, rows, ct.byref(n)))
+        self.nbytes = n.value
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=self.device)
+        self.ptr = (self.buf.data_ptr() + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+
+    def run(self, nlaunch: int = 1) -> None:
+        _check(self.lib, self.lib.psc_xpass_probe(self.N, self.precision, self.rows, ct.c_void_p(self.ptr),
+                                                  self.nbytes, ct.c_void_p(self.stream.cuda_stream), nlaunch))

@@ -880,6 +880,100 @@ psc_status psc_time(psc_sim* s, double* t, int64_t* step, double* dt) {
 
 }  // extern "C"
 
+// ---------------------------------------------------------------- X-pass probe
+
+namespace {
+
+// Deterministic input pattern of the probe: values in [-1, 1) scaled to the
+// magnitude of unnormalised coefficients, from a 64-bit mix of the index.
+template <typename T>
+__global__ void k_probe_fill(T* p, long long n, T amp) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = (unsigned long long)i * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    z = (z ^ (z >> 31)) * 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 29;
+    p[i] = amp * (T)((double)(z >> 11) * 0x1.0p-52 - 1.0);
+  }
+}
+
+struct ProbeLayout {
+  size_t ctrl, tw, yb, xb, total;
+};
+
+ProbeLayout probe_layout(const Dims& d, int fp64, long long rows) {
+  const size_t cs = fp64 ? 16 : 8;
+  ProbeLayout L;
+  size_t o = 0;
+  auto take = [&](size_t b) { size_t r = o; o = align256(o + b); return r; };
+  L.ctrl = take(sizeof(Ctrl));
+  L.tw = take((size_t)d.N * cs);
+  L.yb = take((size_t)Y_NSTREAM_ROT * rows * d.M * cs);
+  L.xb = take((size_t)4 * rows * d.M * cs);
+  L.total = o;
+  return L;
+}
+
+psc_status probe_check(int32_t N, int32_t precision, int64_t rows) {
+  if (!size_supported(N) || N == 520) return fail(PSC_EUNSUPPORTED_N, "probe: unsupported N");
+  if (precision != PSC_FP64 && precision != PSC_FP32_MIXED) return fail(PSC_EINVAL, "probe: bad precision");
+  if (rows <= 0 || rows % 64 != 0 || rows > (int64_t)N * N)
+    return fail(PSC_EINVAL, "probe: rows must be a positive multiple of 64, at most N*N");
+  return PSC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+psc_status psc_xpass_probe_bytes(int32_t N, int32_t precision, int64_t rows, size_t* bytes) {
+  psc_status st = probe_check(N, precision, rows);
+  if (st != PSC_OK) return st;
+  if (!bytes) return fail(PSC_EINVAL, "null bytes");
+  *bytes = probe_layout(make_dims(N), precision == PSC_FP64, rows).total;
+  return PSC_OK;
+}
+
+psc_status psc_xpass_probe(int32_t N, int32_t precision, int64_t rows, void* buf, size_t bytes, void* stream,
+                           int32_t nlaunch) {
+  psc_status st = probe_check(N, precision, rows);
+  if (st != PSC_OK) return st;
+  const int fp64 = precision == PSC_FP64;
+  Dims d = make_dims(N);
+  const ProbeLayout L = probe_layout(d, fp64, rows);
+  if (!buf || ((uintptr_t)buf & 255) != 0 || bytes < L.total || nlaunch < 0)
+    return fail(PSC_EINVAL, "probe: buffer must be 256-byte aligned and psc_xpass_probe_bytes() long; nlaunch >= 0");
+  const cudaStream_t cs = (cudaStream_t)stream;
+  unsigned char* b = (unsigned char*)buf;
+  std::vector<double> twd(2 * (size_t)N);
+  for (int j = 0; j < N; ++j) twiddle(j, N, &twd[2 * j], &twd[2 * j + 1]);
+  std::vector<float> twf(twd.begin(), twd.end());
+  Ctrl c0;
+  std::memset(&c0, 0, sizeof(c0));
+  PSC_CUDA(cudaMemcpyAsync(b + L.ctrl, &c0, sizeof(c0), cudaMemcpyHostToDevice, cs));
+  if (fp64) PSC_CUDA(cudaMemcpyAsync(b + L.tw, twd.data(), twd.size() * 8, cudaMemcpyHostToDevice, cs));
+  else PSC_CUDA(cudaMemcpyAsync(b + L.tw, twf.data(), twf.size() * 4, cudaMemcpyHostToDevice, cs));
+  const long long nre = 2LL * Y_NSTREAM_ROT * rows * d.M;
+  const double amp = 0.05 * (double)N * N * N;
+  if (fp64) k_probe_fill<double><<<152 * 8, 256, 0, cs>>>((double*)(b + L.yb), nre, amp);
+  else k_probe_fill<float><<<152 * 8, 256, 0, cs>>>((float*)(b + L.yb), nre, (float)amp);
+  PSC_LAUNCHED("psc_xpass_probe: fill");
+  d.ys = (long long)rows * d.M;  // the X pass reads rows and stream strides from here
+  PassArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.d = d;
+  a.yb = b + L.yb;
+  a.xb = b + L.xb;
+  a.tw = b + L.tw;
+  a.ctrl = (Ctrl*)(b + L.ctrl);
+  a.st = cs;
+  const PassTable* tb = fp64 ? table_f64(N) : table_f32(N);
+  for (int i = 0; i < nlaunch; ++i) tb->xpass(a, XMODE_RHS);
+  PSC_LAUNCHED("psc_xpass_probe");
+  return PSC_OK;
+}
+
+}  // extern "C"
+
 struct psc_batch {
   std::vector<psc_sim*> sims;
   std::vector<int64_t> launches_per_step;

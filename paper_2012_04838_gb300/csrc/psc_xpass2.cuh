@@ -429,8 +429,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : PSC_X2_MINB) k_xpass
   C* __restrict__ xb = static_cast<C*>(a.xb);
   const C* __restrict__ tw = static_cast<const C*>(a.tw);
   x2_twiddles<T, N>(reinterpret_cast<C*>(smraw + XC::LINE_BYTES * ROWS + XC::ACC_BYTES), tw, q);
-  const long long ys = (long long)N * N * M;
-  const long long nlines = (long long)N * N;
+  // rows and the stream stride come from the arguments (N*N rows for a pass over the box)
+  const long long ys = a.d.ys;
+  const long long nlines = ys / M;
   const T scale = T(1.0 / ((double)N * N * N));
   const C zero = mk(T(0), T(0));
   // maximum of |u1|+|u2|+|u3| over the thread's points (unscaled fields in the
@@ -440,7 +441,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : PSC_X2_MINB) k_xpass
 
 #pragma unroll 1
   for (long long base = (long long)blockIdx.x * ROWS; base < nlines; base += (long long)gridDim.x * ROWS) {
-    const long long line = base + lid;  // N*N is a multiple of ROWS
+    const long long line = base + lid;  // the row count (N*N, or a probe's multiple of 64) is a multiple of ROWS
     const C* __restrict__ row = yb + line * M;
     auto Y = [&](int s, int kx) -> C {
       if (!PSC_OK_INDEX(s * ys + line * M + kx, (long long)Y_NSTREAM * ys, a.ctrl)) return zero;
@@ -619,8 +620,8 @@ __global__ void __launch_bounds__(X2SCfg<T, N>::THREADS, 1) k_xpass2s(PassArgs a
     mbar_init_fence();
   }
   x2_twiddles<T, N>(reinterpret_cast<C*>(smraw + SC::TW_OFF), static_cast<const C*>(a.tw), q);
-  const long long ys = (long long)N * N * M;
-  const long long nlines = (long long)N * N;
+  const long long ys = a.d.ys;  // N*N*M for a pass over the box
+  const long long nlines = ys / M;
   const long long stride = (long long)gridDim.x * ROWS;
   const T scale = T(1.0 / ((double)N * N * N));
   const bool leader = q.tid == 0;
