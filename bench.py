@@ -39,13 +39,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--N", type=int, default=WORKLOAD["N"])
-    ap.add_argument("--fp64-steps", type=int, default=2, help="timed FP64 companion steps (0 = skip)")
+    ap.add_argument("--fp64-steps", type=int, default=5, help="timed FP64 companion steps (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-cufft", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--form", choices=["rotational", "convective"], default="rotational",
                     help="nonlinear term of the timed workload (default: rotational u x omega)")
     ap.add_argument("--companion", action="store_true",
@@ -212,54 +212,122 @@ def ensemble_requests(seed: int = 4):
     return out
 
 
-def run_ensemble(dev):
-    """The batched ensemble run to completion: every RK4 step of all active boxes is
-    one replay of a captured CUDA graph (rebuilt as boxes finish)."""
+def _per_step_alone(dev, reqs, precision, steps=20):
+    """Seconds per step of each size's first box stepped alone with psc_step."""
     import torch
     import paper_2012_04838_gb300 as psc
-    from paper_2012_04838_gb300.serve import Server, make_params
-    reqs = ensemble_requests()
-    res, summ = Server(budget_bytes=150e9, chunk=10 ** 9, device=dev, records="final").run(reqs)
-    out = {"metric": "ensemble sims/hr", "value": summ["sims_per_hour"], "unit": "sims/hr",
-           "boxes": len(reqs), "total_steps": sum(r.steps for r in reqs), "wall_s": summ["wall_s"],
-           "grid_point_stages_per_s": summ["grid_point_stages_per_s"],
-           "graph_builds": summ["graph_builds"], "graph_build_s": round(summ["graph_build_s"], 3),
-           "records": summ["records"], "precision": "fp32_mixed",
-           "config": "64x64^3 + 16x96^3 + 4x128^3, k_max eta in [1,2], Sc in {0.7,1,2}, "
-                     "200-1000 steps, CFL 0.5, one graph replay per ensemble step, a statistics "
-                     "record of each box when it ends"}
-    # plain FP64 single-run path on the same GPU: each box alone, no batching;
-    # per-step time of one box per size x every box's step count
+    from paper_2012_04838_gb300.serve import make_params
     per_step = {}
-    for N in (64, 96, 128):
+    for N in sorted({r.N for r in reqs}):
         r = next(q for q in reqs if q.N == N)
         p = make_params(r)
-        p.precision = psc.FP64
+        p.precision = precision
         s = psc.Simulation(p, device=dev)
         s.init_field()
         s.step(2)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s.step(20)
+        s.step(steps)
         torch.cuda.synchronize()
-        per_step[N] = (time.perf_counter() - t0) / 20
+        per_step[N] = (time.perf_counter() - t0) / steps
         s.close()
-    est = sum(per_step[r.N] * r.steps for r in reqs)
-    out["fp64_single_run"] = {"sims_per_hour_est": 3600.0 * len(reqs) / est, "wall_s_est": est,
-                              "s_per_step": per_step,
-                              "how": "each box alone in FP64 via psc_step, 20 timed steps per size, "
-                                     "scaled by every box's step count"}
+    return per_step
+
+
+def run_ensemble(dev):
+    """The batched ensemble run to completion, stepped by the persistent kernel
+    (one launch per RK stage over the work table; boxes leave as they finish)
+    and, for comparison, by captured graphs of every member's launches; plus
+    the same boxes one after another, unbatched, in FP32-mixed and FP64
+    (per-size step times x every box's step count)."""
+    import torch
+    import paper_2012_04838_gb300 as psc
+    from paper_2012_04838_gb300.serve import Server
+    reqs = ensemble_requests()
+    res, summ = Server(budget_bytes=150e9, chunk=10 ** 9, device=dev, records="final",
+                       mode="persistent").run(reqs)
+    torch.cuda.empty_cache()
+    out = {"metric": "ensemble sims/hr", "value": summ["sims_per_hour"], "unit": "sims/hr",
+           "boxes": len(reqs), "total_steps": sum(r.steps for r in reqs), "wall_s": summ["wall_s"],
+           "grid_point_stages_per_s": summ["grid_point_stages_per_s"], "mode": summ["mode"],
+           "table_updates": summ["table_updates"], "step_busy_fraction": summ["step_busy_fraction"],
+           "records": summ["records"], "precision": "fp32_mixed",
+           "config": "64x64^3 + 16x96^3 + 4x128^3, k_max eta in [1,2], Sc in {0.7,1,2}, "
+                     "200-1000 steps, CFL 0.5, one persistent launch per RK stage in a captured graph, "
+                     "a statistics record of each box when it ends"}
+    _, sg = Server(budget_bytes=150e9, chunk=10 ** 9, device=dev, records="final", mode="graph").run(reqs)
+    torch.cuda.empty_cache()
+    out["graph_batched"] = {"sims_per_hour": sg["sims_per_hour"], "wall_s": sg["wall_s"],
+                            "grid_point_stages_per_s": sg["grid_point_stages_per_s"],
+                            "graph_builds": sg["graph_builds"],
+                            "how": "every member's kernels captured into one CUDA graph per RK4 step"}
+    for name, prec in (("fp32_sequential", psc.FP32_MIXED), ("fp64_single_run", psc.FP64)):
+        per_step = _per_step_alone(dev, reqs, prec)
+        est = sum(per_step[r.N] * r.steps for r in reqs)
+        out[name] = {"sims_per_hour_est": 3600.0 * len(reqs) / est, "wall_s_est": est, "s_per_step": per_step,
+                     "how": "each box alone via psc_step, 20 timed steps per size, scaled by every box's "
+                            "step count (an estimate)"}
+    out["batching_gain_vs_fp32_sequential"] = out["value"] / out["fp32_sequential"]["sims_per_hour_est"]
     out["speedup_vs_fp64_single_run"] = out["value"] / out["fp64_single_run"]["sims_per_hour_est"]
+    out["persistent_over_graph"] = out["value"] / out["graph_batched"]["sims_per_hour"]
     torch.cuda.empty_cache()
     return out
 
 
-def run_cufft_comparator(dev, N):
-    """Library comparison (not the product): the 9 inverse and 4 forward 3D real
-    transforms one RHS evaluation needs, done with cuFFT through torch.fft on
-    full N^3 grids in FP32, timed with CUDA events.  No pointwise work, no
-    truncation, no projection: a lower bound for a plain cuFFT-based stage."""
+def plain_rhs_torch(state, N, beta=1.0, kF=2.0, eps_inj=0.1):
+    """The right-hand side N(u, phi) of Eqs. 7-8 (2/3 rule, rotational form,
+    constant-power forcing, no linear terms) written the plain way, for
+    comparison only: cuFFT 3D transforms of whole N^3 grids through torch.fft
+    and torch's elementwise kernels, in the precision of `state` (a compact
+    state tensor [4][2K+1][2K+1][K+1]).  Returns the four fields in the full
+    half-spectrum layout [4][N][N][N/2+1].  Library code; not the product."""
     import torch
+    dev, cdt = state.device, state.dtype
+    rdt = torch.float64 if cdt == torch.complex128 else torch.float32
+    K = (N - 1) // 3
+    idx = torch.arange(-K, K + 1, device=dev) % N
+    full = torch.zeros((4, N, N, N // 2 + 1), dtype=cdt, device=dev)
+    full[:, idx[:, None], idx[None, :], :K + 1] = state
+    kf = torch.fft.fftfreq(N, 1.0 / N, device=dev).round().to(rdt)
+    kx = torch.arange(N // 2 + 1, device=dev, dtype=rdt).view(1, 1, -1)
+    ky, kz = kf.view(1, -1, 1), kf.view(-1, 1, 1)
+    keep = (kx <= K) & (ky.abs() <= K) & (kz.abs() <= K)
+    inv = lambda a: torch.fft.irfftn(a, s=(N, N, N))
+    u1, u2, u3 = inv(full[0]), inv(full[1]), inv(full[2])
+    w1 = inv(1j * (ky * full[2] - kz * full[1]))
+    w2 = inv(1j * (kz * full[0] - kx * full[2]))
+    w3 = inv(1j * (kx * full[1] - ky * full[0]))
+    n1 = torch.fft.rfftn(u2 * w3 - u3 * w2) * keep
+    n2 = torch.fft.rfftn(u3 * w1 - u1 * w3) * keep
+    n3 = torch.fft.rfftn(u1 * w2 - u2 * w1) * keep
+    del w1, w2, w3
+    s = u1 * inv(1j * kx * full[3]) + u2 * inv(1j * ky * full[3]) + u3 * inv(1j * kz * full[3])
+    sh = torch.fft.rfftn(s) * keep
+    del u1, u2, u3, s
+    k2 = kx * kx + ky * ky + kz * kz
+    kdot = (kx * n1 + ky * n2 + kz * n3) / torch.where(k2 == 0, torch.ones_like(k2), k2)
+    n1, n2, n3 = n1 - kx * kdot, n2 - ky * kdot, n3 - kz * kdot
+    band = ((k2 > 0) & (k2 <= kF * kF) & keep).to(rdt)
+    w = torch.where(kx == 0, 1.0, 2.0).to(rdt)
+    ef = float((band * w * (full[0].abs() ** 2 + full[1].abs() ** 2 + full[2].abs() ** 2)).sum()) / (2.0 * float(N) ** 6)
+    Ab = band * (eps_inj / (2.0 * ef) if ef > 1e-300 else 0.0)
+    zero = torch.zeros((), dtype=cdt, device=dev)
+    out = torch.stack([torch.where(k2 == 0, zero, n1 + Ab * full[0]),
+                       torch.where(k2 == 0, zero, n2 + Ab * full[1]),
+                       torch.where(k2 == 0, zero, n3 + Ab * full[2]),
+                       -sh - beta * full[1] * keep])
+    return out
+
+
+def run_cufft_comparator(dev, N, sim_state=None):
+    """Library comparison (not the product): one right-hand side written the
+    plain way (plain_rhs_torch: cuFFT through torch.fft on whole grids plus
+    torch elementwise kernels) in FP32 and in FP64, and the 13 bare cuFFT
+    transforms of a stage, timed with CUDA events.  A step is four such
+    evaluations plus stage updates, so 4x the RHS time is a lower bound for a
+    plain cuFFT time step."""
+    import torch
+    out = {}
     torch.cuda.empty_cache()
     try:
         x = torch.randn(N, N, N, device=dev, dtype=torch.float32)
@@ -280,32 +348,93 @@ def run_cufft_comparator(dev, N):
         ms = e0.elapsed_time(e1)
         del x, xh, y, yh
         torch.cuda.empty_cache()
-        return {"ms_per_stage_transforms": ms, "ms_per_step_transforms": 4 * ms,
-                "what": f"cuFFT via torch.fft: 9 irfftn + 4 rfftn of {N}^3 FP32 per RK stage"}
+        out["transforms_fp32"] = {"ms_per_stage": ms, "ms_per_step": 4 * ms,
+                                  "what": f"9 irfftn + 4 rfftn of {N}^3 FP32 per RK stage"}
     except Exception as e:
-        return {"error": str(e)[:200]}
+        out["transforms_fp32"] = {"error": str(e)[:200]}
+    K = (N - 1) // 3
+    for name, cdt in (("rhs_fp32", torch.complex64), ("rhs_fp64", torch.complex128)):
+        try:
+            torch.cuda.empty_cache()
+            g = torch.Generator(device=dev).manual_seed(7)
+            st = (torch.randn((4, 2 * K + 1, 2 * K + 1, K + 1), dtype=cdt, device=dev, generator=g)
+                  * (0.05 * float(N) ** 3 / (1 + K)))
+            plain_rhs_torch(st, N)  # warm-up (cuFFT plans)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = plain_rhs_torch(st, N)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            del r, st
+            torch.cuda.empty_cache()
+            out[name] = {"ms_per_rhs": ms, "steps_per_s_upper_bound": 1000.0 / (4 * ms),
+                         "what": "one plain right-hand side: cuFFT whole-grid transforms + torch elementwise"}
+        except Exception as e:
+            out[name] = {"error": str(e)[:200]}
+    return out
 
 
 def run_serve(dev, n):
     """Poisson arrivals (4/s), N from {64,96,128,192,256}, 100-2000 steps, admitted
-    under a 150 GB budget, stepped together, records every 50 steps."""
+    under a 150 GB budget, stepped together by the persistent kernel, records
+    every 50 steps."""
     import torch
     from paper_2012_04838_gb300.serve import Server, poisson_requests
     reqs = poisson_requests(n, rate=4.0, seed=5)
     res, summ = Server(budget_bytes=150e9, chunk=50, device=dev).run(reqs)
     torch.cuda.empty_cache()
-    return {"requests": summ["requests"], "p50_latency_s": summ["p50_latency_s"],
-            "p99_latency_s": summ["p99_latency_s"], "wall_s": summ["wall_s"],
-            "grid_point_stages_per_s": summ["grid_point_stages_per_s"],
-            "sims_per_hour": summ["sims_per_hour"], "peak_active": summ["peak_active"],
-            "peak_workspace_GB": summ["peak_bytes"] / 1e9, "graph_builds": summ["graph_builds"],
-            "config": f"{n} requests, Poisson 4/s, N in {{64,96,128,192,256}}, 100-2000 steps, "
-                      "k_max eta in [1,2], Sc in {0.7,1,2}, 150 GB budget, FP32-mixed"}
+    keys = ("requests", "p50_latency_s", "p99_latency_s", "wall_s", "grid_point_stages_per_s", "sims_per_hour",
+            "peak_active", "mode", "table_updates", "graph_builds", "chunks", "records", "step_busy_fraction")
+    out = {k: summ[k] for k in keys}
+    out["peak_workspace_GB"] = summ["peak_bytes"] / 1e9
+    out["time_s"] = {"steps_on_gpu": round(summ["step_s"], 3), "records": round(summ["record_s"], 3),
+                     "admission_and_ic": round(summ["admit_s"], 3), "table_or_graph": round(summ["graph_build_s"], 3),
+                     "other_host": round(summ["other_s"], 3)}
+    out["gpu_idle_fraction"] = 1.0 - summ["step_busy_fraction"]
+    out["config"] = (f"{n} requests, Poisson 4/s, N in {{64,96,128,192,256}}, 100-2000 steps, "
+                     "k_max eta in [1,2], Sc in {0.7,1,2}, 150 GB budget, FP32-mixed, records every 50 steps")
+    return out
 
 
 # ---------------------------------------------------------------- reference arm
 
+def _oracle_steps_worker(args):
+    """One process of the all-cores oracle timing: `nsteps` steps at N^3."""
+    N, nsteps = args
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    sps, el = oracle_steps_per_s(nsteps, N)
+    return sps, el
+
+
+def oracle_sweep(sizes=(32, 64, 128, 256), all_cores_N=128):
+    """The FP64 oracle's step rate on this host: single-threaded at each size,
+    and over all host cores as independent replicas at all_cores_N."""
+    import multiprocessing as mp
+    single = {}
+    for N in sizes:
+        n = 1 if N >= 256 else 2
+        sps, el = oracle_steps_per_s(n, N)
+        single[N] = {"steps_per_s": sps, "steps": n, "seconds": round(el, 3)}
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        rates = pool.map(_oracle_steps_worker, [(all_cores_N, 1)] * cores)
+    wall = time.perf_counter() - t0
+    slowest = max(el for _, el in rates)
+    return {"nproc": cores, "single_thread": single,
+            "all_cores": {"N": all_cores_N, "replicas": cores, "steps_per_s": cores / slowest,
+                          "wall_s_with_startup": round(wall, 2),
+                          "how": "one oracle step per process, one process per core, rate = replicas / slowest"}}
+
+
 def run_reference(a):
+    """The reference arm: the FP64 CPU oracle, as it stands, on this host.
+    Each step is one oracle RK4 step at 128^3, a bounded sample of the 1024^3
+    workload; ms_per_step is the measured time of those steps, and `value`
+    models the 1024^3 rate from it by the N^3 log2 N work of a step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
@@ -322,24 +451,26 @@ def run_reference(a):
     for _ in range(a.steps):
         uh, ph = O.step(uh, ph, g, p, dt)
     el = time.perf_counter() - t0
+    measured = a.steps / el
     scale = oracle_scale(N, a.N)
-    val = a.steps / el / scale
-    sample = (f"each step = one FP64 oracle RK4 step at {N}^3 (NumPy, 1 thread), scaled to {a.N}^3 "
-              f"by N^3 log2 N (x{scale:.1f})")
+    val = measured / scale
+    sweep = oracle_sweep()
+    sample = (f"each step = one FP64 oracle RK4 step at {N}^3 (NumPy, 1 thread); the {a.N}^3 value is "
+              f"modelled from it by N^3 log2 N (x{scale:.1f})")
     out = {"impl": "reference", "metric": "RK4 steps/s", "value": val, "unit": "steps/s",
-           "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
-           "ms_per_step": 1000.0 / val, "higher_is_better": True, "scaling": "weak",
+           "value_is": f"modelled: measured {N}^3 steps/s / {scale:.1f}",
+           "measured": {"N": N, "steps": a.steps, "steps_per_s": measured, "ms_per_step": 1000.0 / measured},
+           "scale": scale, "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+           "ms_per_step": 1000.0 / measured, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": f"{a.N}^3 forced HIT + passive scalar (oracle sample at {N}^3)",
                       "N": a.N, "sample_N": N},
-           "cpu_baseline": {"value": val, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                            "sample": sample},
+           "oracle_sweep": sweep,
+           "cpu_baseline": {"value": val, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": val, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
 
-
-# ---------------------------------------------------------------- our arm
 
 def run_long(N=256, steps=2000, every=10):
     """FP32-mixed and FP64 from the same IC, side by side: time-averaged E(k)
@@ -734,18 +865,37 @@ def main():
             torch.cuda.synchronize()
             f0 = torch.cuda.Event(enable_timing=True)
             f1 = torch.cuda.Event(enable_timing=True)
-            f0.record(s64.stream)
-            s64.step(a.fp64_steps)
-            f1.record(s64.stream)
-            torch.cuda.synchronize()
+            with ClockSampler(dev.index) as clk64:
+                f0.record(s64.stream)
+                s64.step(a.fp64_steps)
+                f1.record(s64.stream)
+                torch.cuda.synchronize()
             fms = f0.elapsed_time(f1) / a.fp64_steps
             out["fp64"] = {"steps_per_s": 1000.0 / fms, "ms_per_step": fms, "steps": a.fp64_steps,
-                           "mixed_over_fp64": value / (world * 1000.0 / fms)}
+                           "mixed_over_fp64": value / (world * 1000.0 / fms), "clocks": clk64.summary(),
+                           "what": "the same workload in FP64, steps without records"}
             s64.close()
             del s64
             torch.cuda.empty_cache()
         except Exception as e:  # report, do not hide
             out["fp64"] = {"error": str(e)[:200]}
+
+    # FMA peaks of this device (the ALU roofline of the FP32 X pass and of the FP64 path)
+    try:
+        f32 = psc.binding.fma_peak_tflops(psc.FP32_MIXED, dev, iters=2000)
+        f64 = psc.binding.fma_peak_tflops(psc.FP64, dev, iters=100)
+        xflops = 6.5 * 5 * N * math.log2(N) * N * N  # 4.5 inverse + 2 forward complex transforms per row
+        xms = per_kernel.get("xpass", {}).get("ms_per_launch")
+        out["alu"] = {"fp32_fma_tflops": round(f32, 2), "fp64_fma_tflops": round(f64, 3),
+                      "how": "psc_fma_probe: 8 independent FMA chains per thread, 8 CTAs of 256 per SM, best of 3",
+                      "xpass_nominal_tflops": round(xflops / (xms / 1000.0) / 1e12, 2) if xms else None,
+                      "xpass_nominal_flops": xflops}
+        if "fp64" in out and "ms_per_step" in out["fp64"]:
+            fl = 4 * 13.3 * 5 * N ** 3 * math.log2(N)  # transforms of one step, 5 N log2 N per line
+            out["alu"]["fp64_path_nominal_tflops"] = round(fl / (out["fp64"]["ms_per_step"] / 1000.0) / 1e12, 3)
+            out["alu"]["fp64_path_frac_of_fp64_peak"] = round(out["alu"]["fp64_path_nominal_tflops"] / f64, 3)
+    except Exception as e:
+        out["alu"] = {"error": str(e)[:200]}
 
     if not a.no_cufft:
         out["cufft_comparator"] = run_cufft_comparator(dev, N)
@@ -759,6 +909,10 @@ def main():
         sps, el = oracle_steps_per_s(2)
         sc = oracle_scale(ORACLE_SAMPLE_N, N)
         out["cpu_baseline"] = {"value": sps / sc, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                               "value_is": f"modelled from the measured {ORACLE_SAMPLE_N}^3 rate",
+                               "measured": {"N": ORACLE_SAMPLE_N, "steps": 2, "steps_per_s": sps,
+                                            "seconds": round(el, 2)},
+                               "scale": sc,
                                "sample": f"2 FP64 oracle RK4 steps at {ORACLE_SAMPLE_N}^3 "
                                          f"({el:.1f} s, NumPy single thread), scaled to {N}^3 by "
                                          f"N^3 log2 N (x{sc:.1f})"}

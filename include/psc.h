@@ -199,6 +199,45 @@ psc_status psc_batch_create(psc_sim* const* sims, int32_t n, void* stream, psc_b
 psc_status psc_batch_step(psc_batch* b, int32_t nsteps); /* asynchronous on `stream` */
 psc_status psc_batch_destroy(psc_batch* b);
 
+/* Persistent ensembles: one launch per RK stage over a device work table.
+ *
+ * The paper runs an ensemble as separate serial runs (Table 2); this batched
+ * form is an addition for many small boxes.  psc_batch_create_persistent()
+ * captures, into one CUDA graph, a reset of the table's counters and four
+ * launches of a persistent kernel, one per RK4 stage; each launch steps every
+ * member through that stage (forcing amplitude, the five transform passes,
+ * the CFL reset of Eq. 10 at stage 1, the stage combine, and after stage 4 the
+ * deterministic forcing), its CTAs taking (box, pass, tile) items from the
+ * work table in pass order.  An item waits until every tile of its box's
+ * previous pass has completed; such a wait is bounded (about two seconds),
+ * after which the step is abandoned and the member reports PSC_ETIMEOUT at its
+ * next statistics call.  Each member advances bit for bit as psc_step() would
+ * advance it alone.
+ *
+ * Members: FP32-mixed, 2/3 rule, rotational form, N in {32, 48, 64, 96, 128,
+ * 192, 256} and N <= max_N (max_N sets the kernel's shared memory, so keep it
+ * as small as the ensemble allows); otherwise PSC_EINVAL / PSC_EUNSUPPORTED_N.
+ * dev_table: caller-owned device memory of psc_batch_table_bytes(max_boxes)
+ * bytes, 256-byte aligned, kept until psc_batch_destroy().  stream: non-NULL;
+ * every batch step and table update runs on it (members' own streams are not
+ * used by the batch).
+ *
+ * psc_batch_set_members() replaces the member list (up to max_boxes, 0 allowed)
+ * by rewriting the table on `stream`, ordered after the steps already
+ * enqueued; the captured graph stays valid, so boxes join and leave between
+ * steps without a new capture.  Members must not be used on their own while a
+ * batch step may be running (synchronise `stream` first).  psc_batch_step()
+ * and psc_batch_destroy() serve both kinds of batch. */
+#define PSC_BATCH_MAX_BOXES 4096
+typedef enum { PSC_BATCH_GRAPH = 0, PSC_BATCH_PERSISTENT = 1 } psc_batch_mode;
+psc_status psc_batch_table_bytes(int32_t max_boxes, size_t* bytes);
+psc_status psc_batch_create_persistent(psc_sim* const* sims, int32_t n, int32_t max_boxes, int32_t max_N,
+                                       void* dev_table, size_t table_bytes, void* stream, psc_batch** out);
+psc_status psc_batch_set_members(psc_batch* b, psc_sim* const* sims, int32_t n);
+/* The batch's kind (psc_batch_mode), its persistent grid (CTAs; 0 for a graph
+ * batch) and the kernel launches its steps have made (persistent batches). */
+psc_status psc_batch_info(const psc_batch* b, int32_t* mode, int32_t* grid, int64_t* launches);
+
 /* Kernel classes for profiling. */
 typedef enum {
   PSC_K_FORCING = 0,  /* band energy and forcing amplitude                   */
@@ -283,6 +322,14 @@ psc_status psc_shell_spectra_noalloc(const void* state, int32_t N, int32_t preci
 psc_status psc_xpass_probe_bytes(int32_t N, int32_t precision, int64_t rows, size_t* bytes);
 psc_status psc_xpass_probe(int32_t N, int32_t precision, int64_t rows, void* buf, size_t bytes, void* stream,
                            int32_t nlaunch);
+
+/* Measurement aid (no counterpart in the paper): `blocks` CTAs of 256 threads
+ * each run 8 independent chains of 128 * iters fused multiply-adds in FP32
+ * (PSC_FP32_MIXED) or FP64, storing one value per thread to the device buffer
+ * `out` (blocks * 256 elements).  2 * 8 * 128 * iters * 256 * blocks floating-
+ * point operations; timed by the caller, it gives the device's FMA peak that
+ * the FP32 and FP64 paths are compared against.  Asynchronous on `stream`. */
+psc_status psc_fma_probe(int32_t precision, int32_t iters, int32_t blocks, void* out, void* stream);
 
 /* Message for the last failing call on this thread (never NULL). */
 const char* psc_last_error(void);

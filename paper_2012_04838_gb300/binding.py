@@ -74,6 +74,11 @@ EXPORTS = [
     ("psc_batch_create", ct.c_int, [ct.POINTER(_VP), ct.c_int32, _VP, ct.POINTER(_VP)]),
     ("psc_batch_step", ct.c_int, [_VP, ct.c_int32]),
     ("psc_batch_destroy", ct.c_int, [_VP]),
+    ("psc_batch_table_bytes", ct.c_int, [ct.c_int32, ct.POINTER(_SZ)]),
+    ("psc_batch_create_persistent", ct.c_int, [ct.POINTER(_VP), ct.c_int32, ct.c_int32, ct.c_int32, _VP, _SZ,
+                                               _VP, ct.POINTER(_VP)]),
+    ("psc_batch_set_members", ct.c_int, [_VP, ct.POINTER(_VP), ct.c_int32]),
+    ("psc_batch_info", ct.c_int, [_VP, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int64)]),
     ("psc_profile_enable", ct.c_int, [_VP, ct.c_int32]),
     ("psc_profile_read", ct.c_int, [_VP, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.c_int32]),
     ("psc_launch_count", ct.c_int, [_VP, ct.POINTER(ct.c_int64)]),
@@ -85,6 +90,7 @@ EXPORTS = [
                                              ct.POINTER(ct.c_double), ct.c_int32, _VP]),
     ("psc_xpass_probe_bytes", ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int64, ct.POINTER(_SZ)]),
     ("psc_xpass_probe", ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int64, _VP, _SZ, _VP, ct.c_int32]),
+    ("psc_fma_probe", ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int32, _VP, _VP]),
     ("psc_last_error", ct.c_char_p, []),
 ]
 
@@ -312,6 +318,66 @@ class Simulation:
         return t.value, n.value, dt.value
 
 
+PERSISTENT_SIZES = (32, 48, 64, 96, 128, 192, 256)
+BATCH_GRAPH, BATCH_PERSISTENT = 0, 1
+
+
+class PersistentBatch:
+    """Members stepped by one persistent launch per RK stage over a device work
+    table (psc_batch_create_persistent); members can be replaced between steps
+    (set_members) without a new graph capture.  Members: FP32-mixed, 2/3 rule,
+    rotational form, N in PERSISTENT_SIZES and N <= max_N."""
+
+    def __init__(self, sims, max_boxes: int, max_N: int, device=None, stream=None):
+        import torch
+        self.lib = load()
+        self.torch = torch
+        self.device = torch.device(device if device is not None else "cuda")
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        n = ct.c_size_t()
+        _check(self.lib, self.lib.psc_batch_table_bytes(max_boxes, ct.byref(n)))
+        self.nbytes = n.value
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=self.device)
+        self.ptr = (self.buf.data_ptr() + 255) // 256 * 256
+        self.sims = list(sims)
+        arr = (ct.c_void_p * max(1, len(self.sims)))(*[s._h.value for s in self.sims])
+        self._h = ct.c_void_p()
+        for s in self.sims:
+            s.stream.synchronize()
+        with torch.cuda.device(self.device):
+            _check(self.lib, self.lib.psc_batch_create_persistent(arr, len(self.sims), max_boxes, max_N,
+                                                                  ct.c_void_p(self.ptr), self.nbytes,
+                                                                  ct.c_void_p(self.stream.cuda_stream),
+                                                                  ct.byref(self._h)))
+
+    def set_members(self, sims) -> None:
+        self.sims = list(sims)
+        arr = (ct.c_void_p * max(1, len(self.sims)))(*[s._h.value for s in self.sims])
+        _check(self.lib, self.lib.psc_batch_set_members(self._h, arr, len(self.sims)))
+
+    def step(self, n: int = 1) -> None:
+        _check(self.lib, self.lib.psc_batch_step(self._h, n))
+
+    def synchronize(self) -> None:
+        self.stream.synchronize()
+
+    def info(self) -> dict:
+        mode, grid, launches = ct.c_int32(), ct.c_int32(), ct.c_int64()
+        _check(self.lib, self.lib.psc_batch_info(self._h, ct.byref(mode), ct.byref(grid), ct.byref(launches)))
+        return {"mode": mode.value, "grid": grid.value, "launches": launches.value}
+
+    def close(self) -> None:
+        if self._h:
+            self.lib.psc_batch_destroy(self._h)
+            self._h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Batch:
     """Members stepped together through one captured CUDA graph per step.
 
@@ -373,3 +439,28 @@ class XPassProbe:
     def run(self, nlaunch: int = 1) -> None:
         _check(self.lib, self.lib.psc_xpass_probe(self.N, self.precision, self.rows, ct.c_void_p(self.ptr),
                                                   self.nbytes, ct.c_void_p(self.stream.cuda_stream), nlaunch))
+
+
+def fma_peak_tflops(precision: int, device=None, iters: int = 2000, repeats: int = 3) -> float:
+    """FMA throughput of the device in TFLOP/s (psc_fma_probe, best of
+    `repeats` launches of 8 CTAs per SM, CUDA events)."""
+    import torch
+    lib = load()
+    dev = torch.device(device if device is not None else "cuda")
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = 8 * sms
+    out = torch.empty(blocks * 256, dtype=torch.float64 if precision == FP64 else torch.float32, device=dev)
+    st = torch.cuda.current_stream(dev)
+    _check(lib, lib.psc_fma_probe(precision, 10, blocks, ct.c_void_p(out.data_ptr()), ct.c_void_p(st.cuda_stream)))
+    best = None
+    for _ in range(repeats):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        _check(lib, lib.psc_fma_probe(precision, iters, blocks, ct.c_void_p(out.data_ptr()),
+                                      ct.c_void_p(st.cuda_stream)))
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    flops = 2.0 * 8 * 128 * iters * 256 * blocks
+    return flops / (best / 1000.0) / 1e12

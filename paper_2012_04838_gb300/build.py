@@ -73,9 +73,14 @@ def build(checked: bool | None = None, jobs: int | None = None, verbose: bool = 
             obj = os.path.join(odir, f"inst_{t}_{n}.o")
             units.append((obj, [cc] + flags + [f"-DPSC_INST_T={t}", f"-DPSC_INST_N={n}", "-c",
                                                os.path.join(CSRC, "psc_inst.cu"), "-o", obj]))
-    for src in ("psc_capi", "psc_noalloc"):
+    for src in ("psc_capi", "psc_noalloc", "psc_batch"):
         obj = os.path.join(odir, src + ".o")
         units.append((obj, [cc] + flags + ["-c", os.path.join(CSRC, src + ".cu"), "-o", obj]))
+    # the persistent ensemble kernel, one unit per RK stage
+    for stage in (1, 2, 3, 4):
+        obj = os.path.join(odir, f"batch_stage_{stage}.o")
+        units.append((obj, [cc] + flags + [f"-DPSCB_STAGE={stage}", "-c", os.path.join(CSRC, "psc_batch_stage.cu"),
+                                           "-o", obj]))
     todo = [(o, c) for o, c in units if not os.path.exists(o)]
     if todo:
         jobs = jobs or max(1, os.cpu_count() or 1)

@@ -716,7 +716,9 @@ psc_status do_stats(psc_sim* s, double* Ek, double* Ephi, int cap, int* nshell, 
   (void)Vp;
   if ((c.err & 2) || !(umax <= 1.7976931348623157e308))
     return fail(PSC_EUNSTABLE, "non-finite velocity in the CFL monitor");
-  if (c.err & 4) return fail(PSC_ETIMEOUT, "an asynchronous copy into shared memory did not complete in time");
+  if (c.err & 4)
+    return fail(PSC_ETIMEOUT, "a bounded device wait gave up (an asynchronous copy into shared memory, or a "
+                              "dependency of the persistent ensemble kernel, did not complete in time)");
   return PSC_OK;
 }
 
@@ -880,6 +882,44 @@ psc_status psc_time(psc_sim* s, double* t, int64_t* step, double* dt) {
 
 }  // extern "C"
 
+// ---------------------------------------------------------------- ALU probe
+
+namespace {
+
+// Eight independent fused multiply-add chains per thread (enough to hide the
+// pipe latency); the result is stored so nothing is optimised away.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_probe(int iters, T* out) {
+  T a[8];
+  const T b = (T)0.999999, c = (T)1e-7;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = (T)(threadIdx.x + j);
+#pragma unroll 1
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) a[j] = fma(a[j], b, c);
+    }
+  }
+  T s = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += a[j];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace
+
+extern "C" psc_status psc_fma_probe(int32_t precision, int32_t iters, int32_t blocks, void* out, void* stream) {
+  if ((precision != PSC_FP64 && precision != PSC_FP32_MIXED) || iters < 1 || blocks < 1 || !out)
+    return fail(PSC_EINVAL, "psc_fma_probe: bad arguments");
+  const cudaStream_t st = (cudaStream_t)stream;
+  if (precision == PSC_FP64) k_fma_probe<double><<<blocks, 256, 0, st>>>(iters, (double*)out);
+  else k_fma_probe<float><<<blocks, 256, 0, st>>>(iters, (float*)out);
+  PSC_LAUNCHED("psc_fma_probe");
+  return PSC_OK;
+}
+
 // ---------------------------------------------------------------- X-pass probe
 
 namespace {
@@ -981,6 +1021,14 @@ struct psc_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<cudaEvent_t> events;
+  // persistent mode: the device work table and the launch shape baked into the graph
+  int mode = PSC_BATCH_GRAPH;
+  int max_boxes = 0, max_N = 0, grid = 0;
+  size_t smem = 0;
+  void* table = nullptr;
+  std::vector<unsigned char> staging;
+  int64_t launches = 0;  // kernels and memsets the batch's own graph ran
+  bool stall_test = false;  // PSC_BATCH_STALL_TEST=1 at creation (failure-path test)
 };
 
 static void batch_free(psc_batch* b) {
@@ -1054,10 +1102,143 @@ psc_status psc_batch_step(psc_batch* b, int32_t nsteps) {
   for (int k = 0; k < nsteps; ++k) PSC_CUDA(cudaGraphLaunch(b->exec, b->st));
   for (size_t i = 0; i < b->sims.size(); ++i) {
     b->sims[i]->step += nsteps;
-    b->sims[i]->launches += nsteps * b->launches_per_step[i];
+    if (b->mode == PSC_BATCH_GRAPH) b->sims[i]->launches += nsteps * b->launches_per_step[i];
   }
+  if (b->mode == PSC_BATCH_PERSISTENT) b->launches += 4LL * nsteps;
   return PSC_OK;
 }
+
+// ---------------------------------------------------------------- persistent ensembles
+
+static psc_status persistent_member_ok(const psc_sim* m, int max_N) {
+  if (!m) return fail(PSC_EINVAL, "psc_batch: null member");
+  if (m->fp64 || m->d.sph || m->p.nonlinear_form != PSC_NL_ROTATIONAL)
+    return fail(PSC_EINVAL, "persistent batch: members must be FP32-mixed, 2/3 rule, rotational form");
+  if (!pscb_size_supported(m->d.N) || m->d.N > max_N)
+    return fail(PSC_EUNSUPPORTED_N, "persistent batch: N=" + std::to_string(m->d.N) +
+                                        " not among the persistent sizes up to max_N=" + std::to_string(max_N));
+  return PSC_OK;
+}
+
+static PscBatchBox box_of(psc_sim* s) {
+  PscBatchBox b;
+  std::memset(&b, 0, sizeof(b));
+  b.N = s->d.N;
+  b.K = s->d.K;
+  b.M = s->d.M;
+  b.P = s->d.P;
+  b.S = s->d.S;
+  b.zs = s->d.zs;
+  b.ys = s->d.ys;
+  b.U = s->ws + s->L.U;
+  b.V = s->ws + s->L.V;
+  b.Acc = s->ws + s->L.Acc;
+  b.zreg = s->ws + s->L.zreg;
+  b.yreg = s->ws + s->L.yreg;
+  b.eu = s->ws + s->L.eu;
+  b.ep = s->ws + s->L.ep;
+  b.tw = s->ws + s->L.tw;
+  b.ctrl = s->ctrl;
+  const CombineArgs c = combine_args(s, nullptr);
+  b.kF2 = c.kF2;
+  b.kF2_floor = c.kF2_floor;
+  b.eps_inj = s->p.eps_inj;
+  b.beta = c.beta;
+  b.nu = c.nu;
+  b.D = c.D;
+  b.cfl = s->p.cfl;
+  b.dx = 2.0 * M_PI / s->p.N;
+  b.forcing = s->p.forcing;
+  b.integrator = s->p.integrator;
+  b.scalar_on = s->p.scalar_on;
+  b.record_every = s->p.record_every;
+  b.cfl_on = s->p.cfl > 0.0 ? 1 : 0;
+  return b;
+}
+
+static psc_status persistent_upload(psc_batch* b, psc_sim* const* sims, int n) {
+  std::vector<PscBatchBox> boxes;
+  for (int i = 0; i < n; ++i) {
+    psc_status st = persistent_member_ok(sims[i], b->max_N);
+    if (st != PSC_OK) return st;
+    for (int j = 0; j < i; ++j)
+      if (sims[j] == sims[i]) return fail(PSC_EINVAL, "psc_batch: members must be distinct");
+    boxes.push_back(box_of(sims[i]));
+  }
+  PSC_CUDA(pscb_upload(b->table, b->staging.data(), b->max_boxes, boxes.data(), n, b->st, b->stall_test));
+  b->sims.assign(sims, sims + n);
+  b->launches_per_step.assign(n, 0);
+  return PSC_OK;
+}
+
+extern "C" {
+
+psc_status psc_batch_table_bytes(int32_t max_boxes, size_t* bytes) {
+  if (max_boxes < 1 || max_boxes > PSC_BATCH_MAX_BOXES || !bytes)
+    return fail(PSC_EINVAL, "psc_batch_table_bytes: max_boxes in 1..PSC_BATCH_MAX_BOXES and non-null bytes");
+  *bytes = pscb_table_bytes(max_boxes);
+  return PSC_OK;
+}
+
+psc_status psc_batch_create_persistent(psc_sim* const* sims, int32_t n, int32_t max_boxes, int32_t max_N,
+                                       void* dev_table, size_t table_bytes, void* stream, psc_batch** out) {
+  if (!sims || n < 0 || !out || !stream || !dev_table)
+    return fail(PSC_EINVAL, "psc_batch_create_persistent: null argument or negative n");
+  if (max_boxes < 1 || max_boxes > PSC_BATCH_MAX_BOXES || n > max_boxes)
+    return fail(PSC_EINVAL, "psc_batch_create_persistent: need n <= max_boxes <= PSC_BATCH_MAX_BOXES");
+  if (!pscb_size_supported(max_N)) return fail(PSC_EUNSUPPORTED_N, "psc_batch_create_persistent: bad max_N");
+  if (((uintptr_t)dev_table & 255) != 0 || table_bytes < pscb_table_bytes(max_boxes))
+    return fail(PSC_EINVAL, "psc_batch_create_persistent: table must be 256-byte aligned and "
+                            "psc_batch_table_bytes() long");
+  psc_batch* b = new (std::nothrow) psc_batch();
+  if (!b) return fail(PSC_EINVAL, "host allocation failed");
+  b->mode = PSC_BATCH_PERSISTENT;
+  b->st = (cudaStream_t)stream;
+  b->max_boxes = max_boxes;
+  b->max_N = max_N;
+  b->table = dev_table;
+  b->staging.resize(pscb_table_bytes(max_boxes));
+  b->smem = pscb_smem_bytes(max_N);
+  b->grid = pscb_grid(max_N, b->smem);
+  {
+    // test knob: one dependency of stage 1 is never met, so its bounded wait
+    // runs out and the members report PSC_ETIMEOUT (the failure path)
+    const char* e = std::getenv("PSC_BATCH_STALL_TEST");
+    b->stall_test = e && e[0] == '1';
+  }
+  psc_status st = persistent_upload(b, sims, n);
+  if (st != PSC_OK) { batch_free(b); return st; }
+  // one ensemble step: a counter reset and one persistent launch per RK stage
+  cudaError_t e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    const cudaError_t e1 = pscb_step(b->table, b->max_boxes, b->max_N, b->grid, b->smem, b->st);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->st, &g);
+    if (e == cudaSuccess) e = e1;
+    if (e == cudaSuccess) { b->graph = g; e = cudaGraphInstantiate(&b->exec, g, 0); }
+    else if (g) cudaGraphDestroy(g);
+  }
+  if (e != cudaSuccess) { batch_free(b); return cuda_fail(e, "psc_batch_create_persistent: graph capture"); }
+  *out = b;
+  return PSC_OK;
+}
+
+psc_status psc_batch_set_members(psc_batch* b, psc_sim* const* sims, int32_t n) {
+  if (!b || (n > 0 && !sims) || n < 0) return fail(PSC_EINVAL, "psc_batch_set_members: null batch or members");
+  if (b->mode != PSC_BATCH_PERSISTENT) return fail(PSC_EINVAL, "psc_batch_set_members: persistent batches only");
+  if (n > b->max_boxes) return fail(PSC_EINVAL, "psc_batch_set_members: more members than max_boxes");
+  return persistent_upload(b, sims, n);
+}
+
+psc_status psc_batch_info(const psc_batch* b, int32_t* mode, int32_t* grid, int64_t* launches) {
+  if (!b) return fail(PSC_EINVAL, "null batch");
+  if (mode) *mode = b->mode;
+  if (grid) *grid = b->mode == PSC_BATCH_PERSISTENT ? b->grid : 0;
+  if (launches) *launches = b->launches;
+  return PSC_OK;
+}
+
+}  // extern "C"
 
 psc_status psc_batch_destroy(psc_batch* b) {
   if (b) batch_free(b);

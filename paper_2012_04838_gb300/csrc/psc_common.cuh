@@ -87,6 +87,25 @@ template <int N> struct PlanD : Plan<N> {
   static_assert(32 % TPL == 0, "a line's threads must sit inside one warp");
 };
 
+// Thread and block coordinates of a kernel body: the hardware's in an ordinary
+// launch, or virtual ones when the persistent ensemble kernel runs the body as
+// one item of its work table (then the body must not rely on gridDim beyond gdx).
+struct Tctx {
+  int tx, ty, bx, by, bdx, bdy, gdx;
+  unsigned char* smem;  // the body's dynamic shared memory
+};
+__device__ __forceinline__ Tctx hw_ctx(unsigned char* smem) {
+  return Tctx{(int)threadIdx.x, (int)threadIdx.y, (int)blockIdx.x, (int)blockIdx.y,
+              (int)blockDim.x,  (int)blockDim.y,  (int)gridDim.x,  smem};
+}
+
+// Pointer qualifier of pass inputs: __restrict__ in ordinary launches.  The
+// persistent ensemble kernel reads buffers that other CTAs of the same launch
+// wrote, so it compiles the bodies without it (no non-coherent loads).
+#ifndef PSC_RESTRICT
+#define PSC_RESTRICT __restrict__
+#endif
+
 // f(std::integral_constant<int, I>) for I = B .. E-1, each index a compile-time constant
 template <int B, int E, class F> __device__ __forceinline__ void static_for(const F& f) {
   if constexpr (B < E) {

@@ -126,3 +126,40 @@ const PassTable* table_f32(int N);
 const PassTable* table_f64(int N);
 
 }  // namespace psc
+
+// ---------------------------------------------------------------------------
+// Persistent ensemble kernel (psc_batch.cu): the plain-data description of one
+// box of its device work table and the host entry points of that file.  The
+// kernel's bodies are compiled in their own namespace there, so only plain
+// types cross between the two files.
+// ---------------------------------------------------------------------------
+struct PscBatchBox {
+  int N, K, M, P;                 // grid and retained half-width (2/3 rule)
+  long long S, zs, ys;            // element counts of the compact, z and y stages
+  void *U, *V, *Acc, *zreg, *yreg;
+  void *eu, *ep;                  // integrating-factor tables
+  const void* tw;                 // twiddles exp(-2 pi i j / N)
+  void* ctrl;                     // the simulation's control block
+  double kF2, eps_inj, beta, nu, D, cfl, dx;
+  int kF2_floor, forcing, integrator, scalar_on, record_every, cfl_on;
+};
+
+// Grid sizes the persistent kernel runs (FP32-mixed, 2/3 rule, rotational form).
+bool pscb_size_supported(int N);
+// Dynamic shared memory the kernel needs for boxes of up to max_N points.
+size_t pscb_smem_bytes(int max_N);
+// Device bytes of a work table for up to max_boxes boxes.
+size_t pscb_table_bytes(int max_boxes);
+// Build the work table of these boxes on the host and copy it to `table`
+// (device) on `st`; `staging` is a host buffer of pscb_table_bytes() bytes
+// that must stay valid until the copy has completed.  stall_test: the first
+// dependency wait of stage 1 can never be met and is bounded at 50 ms instead
+// of two seconds (a test of the failure path).
+cudaError_t pscb_upload(void* table, void* staging, int max_boxes, const PscBatchBox* boxes, int n,
+                        cudaStream_t st, bool stall_test);
+// One ensemble RK4 step: clear the counters, then one persistent launch per stage.
+cudaError_t pscb_step(void* table, int max_boxes, int max_N, int grid, size_t smem, cudaStream_t st);
+// CTAs of the persistent kernel for boxes up to max_N that fit on the device
+// at once with `smem` bytes of dynamic shared memory each.
+int pscb_grid(int max_N, size_t smem);
+

@@ -1,6 +1,7 @@
 // Pointwise spectral kernels: the stage combine (projection, forcing, scalar
 // source, Lawson IF-RK4 update), forcing amplitude, integrating-factor tables,
 // CFL time step, the FP64 statistics reductions and the initial condition.
+// Kernels that are not templates are static: several units compile this header.
 #pragma once
 
 #include "psc_common.cuh"
@@ -45,11 +46,10 @@ __device__ __forceinline__ bool outside_sphere(const Dims& d, long long k2) {
 //   4: U = Acc + dt/6 r
 // For plain RK4 (section 2.2) E1 = E2 = 1 and r carries the linear terms.
 template <typename T, int STAGE>
-__global__ void __launch_bounds__(256) k_combine(CombineArgs c) {
+__device__ __forceinline__ void b_combine(const CombineArgs& c, const long long i) {
   using C = typename CT<T>::type;
   const Dims& d = c.d;
   const long long S = d.S;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (STAGE == 4 && i == 0) {
     c.ctrl->t += c.ctrl->dt;
     c.ctrl->step += 1;
@@ -58,13 +58,13 @@ __global__ void __launch_bounds__(256) k_combine(CombineArgs c) {
   int kx, ky, kz;
   mode_of(d, i, kx, ky, kz);
   const int k2 = kx * kx + ky * ky + kz * kz;
-  const C* __restrict__ rb = static_cast<const C*>(c.rb);
-  const C* __restrict__ vin = static_cast<const C*>(c.vin);
+  const C* PSC_RESTRICT rb = static_cast<const C*>(c.rb);
+  const C* PSC_RESTRICT vin = static_cast<const C*>(c.vin);
   C r0 = rb[i], r1 = rb[S + i], r2 = rb[2 * S + i];
   C r3 = rb[3 * S + i];
   if (c.rb2) {
     // phase-shift dealiasing: the mean of the products of the two grids
-    const C* __restrict__ rc = static_cast<const C*>(c.rb2);
+    const C* PSC_RESTRICT rc = static_cast<const C*>(c.rb2);
     const C q0 = rc[i], q1 = rc[S + i], q2 = rc[2 * S + i], q3 = rc[3 * S + i];
     r0 = mk(T(0.5) * (q0.x + r0.x), T(0.5) * (q0.y + r0.y));
     r1 = mk(T(0.5) * (q1.x + r1.x), T(0.5) * (q1.y + r1.y));
@@ -127,9 +127,9 @@ __global__ void __launch_bounds__(256) k_combine(CombineArgs c) {
     out[3 * S + i] = rp;
     return;
   }
-  C* __restrict__ U = static_cast<C*>(c.U);
-  C* __restrict__ V = static_cast<C*>(c.V);
-  C* __restrict__ Acc = static_cast<C*>(c.Acc);
+  C* PSC_RESTRICT U = static_cast<C*>(c.U);
+  C* PSC_RESTRICT V = static_cast<C*>(c.V);
+  C* PSC_RESTRICT Acc = static_cast<C*>(c.Acc);
   const T h = (T)c.ctrl->dt;
   const C r[4] = {r0, r1, r2, rp};
 #pragma unroll
@@ -155,6 +155,10 @@ __global__ void __launch_bounds__(256) k_combine(CombineArgs c) {
       U[j] = mk(a.x + h / T(6) * rf.x, a.y + h / T(6) * rf.y);
     }
   }
+}
+template <typename T, int STAGE>
+__global__ void __launch_bounds__(256) k_combine(CombineArgs c) {
+  b_combine<T, STAGE>(c, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Modified pressure (section 2.2, Eq. 6) from the transformed pressure inputs
@@ -186,10 +190,9 @@ __global__ void __launch_bounds__(256) k_pressure(Dims d, const void* rb_, void*
 // Band energy E_f = sum_{0<|k|^2<=kF^2} w |u_k|^2 / (2 N^6) of the state `in`
 // in a fixed order (one thread), and A = eps_inj / (2 E_f) (0 if E_f = 0).
 template <typename T>
-__global__ void k_famp(Dims d, const void* in_, Ctrl* ctrl, double kF2, double eps_inj, int forcing,
-                       int step_start) {
+__device__ __forceinline__ void b_famp(Dims d, const void* in_, Ctrl* ctrl, double kF2, double eps_inj, int forcing,
+                                       int step_start) {
   using C = typename CT<T>::type;
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const C* in = static_cast<const C*>(in_);
   int kb = 0;
   while ((double)(kb + 1) * (kb + 1) <= kF2) ++kb;
@@ -214,6 +217,12 @@ __global__ void k_famp(Dims d, const void* in_, Ctrl* ctrl, double kF2, double e
   // the deterministic forcing keeps the rate of its last rescaling in A
   if (forcing != 2) ctrl->A = (forcing == 1 && ef > 1e-300) ? eps_inj / (2.0 * ef) : 0.0;
 }
+template <typename T>
+__global__ void k_famp(Dims d, const void* in_, Ctrl* ctrl, double kF2, double eps_inj, int forcing,
+                       int step_start) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  b_famp<T>(d, in_, ctrl, kF2, eps_inj, forcing, step_start);
+}
 
 // The paper's deterministic forcing (section 2.3), after the last stage of a
 // step: the band 0 < |k|^2 <= kF^2 of the new state is multiplied by
@@ -221,9 +230,8 @@ __global__ void k_famp(Dims d, const void* in_, Ctrl* ctrl, double kF2, double e
 // the first step (Ef0 < 0: the target is taken from this step's start).  A
 // records the equivalent rate ln(f) / dt.  One thread, fixed order.
 template <typename T>
-__global__ void k_hold(Dims d, void* u_, Ctrl* ctrl, double kF2) {
+__device__ __forceinline__ void b_hold(Dims d, void* u_, Ctrl* ctrl, double kF2) {
   using C = typename CT<T>::type;
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
   C* u = static_cast<C*>(u_);
   int kb = 0;
   while ((double)(kb + 1) * (kb + 1) <= kF2) ++kb;
@@ -258,16 +266,24 @@ __global__ void k_hold(Dims d, void* u_, Ctrl* ctrl, double kF2) {
   ctrl->A = log(f) / ctrl->dt;
   ctrl->Ef = ef * f * f;
 }
+template <typename T>
+__global__ void k_hold(Dims d, void* u_, Ctrl* ctrl, double kF2) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  b_hold<T>(d, u_, ctrl, kF2);
+}
 
 // Integrating factors per axis: e(k) = exp(-nu k^2 dt / 2) (and with D), so
 // that exp(-nu |k|^2 dt/2) = e(|kx|) e(|ky|) e(|kz|).  FP64 exp, stored as T.
 template <typename T>
-__global__ void k_iftab(int K, const Ctrl* ctrl, double nu, double D, T* eu, T* ep) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_iftab(int K, const Ctrl* ctrl, double nu, double D, T* eu, T* ep, int k) {
   if (k > K) return;
   const double dt = ctrl->dt;
   eu[k] = (T)exp(-nu * (double)k * k * dt * 0.5);
   ep[k] = (T)exp(-D * (double)k * k * dt * 0.5);
+}
+template <typename T>
+__global__ void k_iftab(int K, const Ctrl* ctrl, double nu, double D, T* eu, T* ep) {
+  b_iftab<T>(K, ctrl, nu, D, eu, ep, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 #ifndef PSC_SHELLS_ONLY
@@ -275,12 +291,15 @@ __global__ void k_iftab(int K, const Ctrl* ctrl, double nu, double D, T* eu, T* 
 // (the step count lives on the device, so the launch sequence of a step never
 // changes and can be captured in a CUDA graph); a non-finite maximum raises the
 // instability flag and leaves dt unchanged.
-__global__ void k_cfl(Ctrl* c, double cfl, double dx, int record_every) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ __forceinline__ void b_cfl(Ctrl* c, double cfl, double dx, int record_every) {
   if (c->step % record_every != 0) return;
   const double m = __longlong_as_double((long long)c->umax_bits);
   if (!(m <= 1.7976931348623157e308)) { c->err |= 2; return; }
   if (m > 0.0) c->dt = cfl * dx / m;
+}
+static __global__ void k_cfl(Ctrl* c, double cfl, double dx, int record_every) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  b_cfl(c, cfl, dx, record_every);
 }
 
 #endif  // PSC_SHELLS_ONLY
@@ -366,7 +385,7 @@ __global__ void __launch_bounds__(256) k_shells(Dims d, const void* u_, const vo
 
 #ifndef PSC_SHELLS_ONLY
 // Sum the X-pass partials over warps in a fixed order.
-__global__ void k_reduce_moments(const double* partials, int nw, Ctrl* ctrl) {
+static __global__ void k_reduce_moments(const double* partials, int nw, Ctrl* ctrl) {
   const int q = threadIdx.x;
   if (q >= NQ) return;
   double s = 0.0;
@@ -396,7 +415,7 @@ __device__ __forceinline__ double uniform_at(unsigned long long seed, unsigned l
 // (ky, kz) > 0 lexicographically; otherwise c = -k), one Box-Muller complex
 // Gaussian per component from stream elements 8 key(c) + 2j, + 2j + 1,
 // projected normal to c; non-canonical modes take the conjugate.
-__global__ void k_ic_draw(Dims d, unsigned long long seed, double2* z) {
+static __global__ void k_ic_draw(Dims d, unsigned long long seed, double2* z) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.S) return;
   int kx, ky, kz;
@@ -433,7 +452,7 @@ __global__ void k_ic_draw(Dims d, unsigned long long seed, double2* z) {
 // Per-shell factors sqrt(E_target(n) / E_raw(n)); E_target follows the chosen
 // shape (0: n^4 exp(-2 (n/4)^2), 2: Eq. 9 with kF), normalised to K0 over the
 // shells that hold modes.  Eraw holds the raw sums w|z|^2 (any common scale).
-__global__ void k_ic_factors(int nshell, const double* Eraw, double norm, double K0, int shape,
+static __global__ void k_ic_factors(int nshell, const double* Eraw, double norm, double K0, int shape,
                              double kF, double* fac) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   auto target = [&](int n) -> double {

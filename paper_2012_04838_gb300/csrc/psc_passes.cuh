@@ -56,11 +56,12 @@ template <typename T, int N, int W> struct StridedSmem {
 // transform; ends with a barrier).
 template <typename T, int N, int W>
 __device__ __forceinline__ typename CT<T>::type* strided_twiddles(unsigned char* smraw,
-                                                                  const typename CT<T>::type* __restrict__ tw) {
+                                                                  const typename CT<T>::type* PSC_RESTRICT tw,
+                                                                  const Tctx& tcx) {
   using C = typename CT<T>::type;
   using PL = PlanD<N>;
   C* t = reinterpret_cast<C*>(smraw + StridedSmem<T, N, W>::EXCH_BYTES);
-  const int nthr = blockDim.x * blockDim.y, me = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthr = tcx.bdx * tcx.bdy, me = tcx.ty * tcx.bdx + tcx.tx;
   for (int i = me; i < N; i += nthr) {
     if constexpr (PL::WIDE) {
       t[i] = tw[i];  // wide lines index wN^(n2 k1) directly
@@ -212,19 +213,18 @@ __device__ __forceinline__ C shift_out(C v, const void* phase, int k) {
 // runtime loop over its stream table), so the instruction footprint stays that
 // of a single two-step FFT however many streams the pass carries.
 template <typename T, int N, bool STATS, int W, int KK = (N - 1) / 3, bool SHIFT = false>
-__global__ void __launch_bounds__(StridedCfg<T, N, W>::THREADS, StridedCfg<T, N, W>::MINB)
-k_zinv(PassArgs a) {
+__device__ __forceinline__ void b_zinv(const PassArgs& a, const Tctx& tcx) {
   using C = typename CT<T>::type;
   constexpr int K = KK, M = KK + 1, P = 2 * KK + 1;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  unsigned char* smraw = tcx.smem;
   C* sm = reinterpret_cast<C*>(smraw);
-  const int w = threadIdx.x, t = threadIdx.y;
-  const int ix = blockIdx.x * W + w;
-  const int iy = blockIdx.y;
+  const int w = tcx.tx, t = tcx.ty;
+  const int ix = tcx.bx * W + w;
+  const int iy = tcx.by;
   const bool act = ix < M;
-  const C* __restrict__ in = static_cast<const C*>(a.in);
-  C* __restrict__ zb = static_cast<C*>(a.zb);
-  const C* tw = strided_twiddles<T, N, W>(smraw, static_cast<const C*>(a.tw));
+  const C* PSC_RESTRICT in = static_cast<const C*>(a.in);
+  C* PSC_RESTRICT zb = static_cast<C*>(a.zb);
+  const C* tw = strided_twiddles<T, N, W>(smraw, static_cast<const C*>(a.tw), tcx);
   const long long S = (long long)P * P * M, zs = (long long)N * P * M;
   const C zero = mk(T(0), T(0));
   // (input field, multiply by i kz, output stream)
@@ -243,7 +243,7 @@ k_zinv(PassArgs a) {
       case 6: f = 3; deriv = true; s = Z_DZPHI; break;
       default: f = 2; deriv = true; s = Z_DZUZ; break;
     }
-    const C* __restrict__ src = in + f * S + (long long)iy * M + ix;
+    const C* PSC_RESTRICT src = in + f * S + (long long)iy * M + ix;
     strided_fft<T, N, W, +1, KK>(
         [&](int p) -> C {
           int kz;
@@ -262,20 +262,26 @@ k_zinv(PassArgs a) {
   }
 }
 
-template <typename T, int N, int YM, int W, int KK = (N - 1) / 3, bool SHIFT = false>
+template <typename T, int N, bool STATS, int W, int KK = (N - 1) / 3, bool SHIFT = false>
 __global__ void __launch_bounds__(StridedCfg<T, N, W>::THREADS, StridedCfg<T, N, W>::MINB)
-k_yinv(PassArgs a) {
+k_zinv(PassArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  b_zinv<T, N, STATS, W, KK, SHIFT>(a, hw_ctx(smraw));
+}
+
+template <typename T, int N, int YM, int W, int KK = (N - 1) / 3, bool SHIFT = false>
+__device__ __forceinline__ void b_yinv(const PassArgs& a, const Tctx& tcx) {
   using C = typename CT<T>::type;
   constexpr int K = KK, M = KK + 1, P = 2 * KK + 1;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  unsigned char* smraw = tcx.smem;
   C* sm = reinterpret_cast<C*>(smraw);
-  const int w = threadIdx.x, t = threadIdx.y;
-  const int ix = blockIdx.x * W + w;
-  const int z = blockIdx.y;
+  const int w = tcx.tx, t = tcx.ty;
+  const int ix = tcx.bx * W + w;
+  const int z = tcx.by;
   const bool act = ix < M;
-  const C* __restrict__ zb = static_cast<const C*>(a.zb);
-  C* __restrict__ yb = static_cast<C*>(a.yb);
-  const C* tw = strided_twiddles<T, N, W>(smraw, static_cast<const C*>(a.tw));
+  const C* PSC_RESTRICT zb = static_cast<const C*>(a.zb);
+  C* PSC_RESTRICT yb = static_cast<C*>(a.yb);
+  const C* tw = strided_twiddles<T, N, W>(smraw, static_cast<const C*>(a.tw), tcx);
   const long long zs = (long long)N * P * M, ys = (long long)N * N * M;
   const C zero = mk(T(0), T(0));
   // (kind, s1, s2, out): kind 0 = s1, 1 = i ky s1, 2 = i ky s1 - s2
@@ -321,20 +327,26 @@ k_yinv(PassArgs a) {
   }
 }
 
-template <typename T, int N, int W, int KK = (N - 1) / 3, bool SHIFT = false>
+template <typename T, int N, int YM, int W, int KK = (N - 1) / 3, bool SHIFT = false>
 __global__ void __launch_bounds__(StridedCfg<T, N, W>::THREADS, StridedCfg<T, N, W>::MINB)
-k_yfwd(PassArgs a) {
+k_yinv(PassArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  b_yinv<T, N, YM, W, KK, SHIFT>(a, hw_ctx(smraw));
+}
+
+template <typename T, int N, int W, int KK = (N - 1) / 3, bool SHIFT = false>
+__device__ __forceinline__ void b_yfwd(const PassArgs& a, const Tctx& tcx) {
   using C = typename CT<T>::type;
   constexpr int K = KK, M = KK + 1, P = 2 * KK + 1;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  unsigned char* smraw = tcx.smem;
   C* sm = reinterpret_cast<C*>(smraw);
-  const int w = threadIdx.x, t = threadIdx.y;
-  const int ix = blockIdx.x * W + w;
-  const int z = blockIdx.y;
+  const int w = tcx.tx, t = tcx.ty;
+  const int ix = tcx.bx * W + w;
+  const int z = tcx.by;
   const bool act = ix < M;
-  const C* __restrict__ xb = static_cast<const C*>(a.xb);
-  C* __restrict__ yf = static_cast<C*>(a.yf);
-  const C* tw = strided_twiddles<T, N, W>(smraw, static_cast<const C*>(a.tw));
+  const C* PSC_RESTRICT xb = static_cast<const C*>(a.xb);
+  C* PSC_RESTRICT yf = static_cast<C*>(a.yf);
+  const C* tw = strided_twiddles<T, N, W>(smraw, static_cast<const C*>(a.tw), tcx);
   const long long zs = (long long)N * P * M, ys = (long long)N * N * M;
   const C zero = mk(T(0), T(0));
 #pragma unroll 1
@@ -358,18 +370,24 @@ k_yfwd(PassArgs a) {
 
 template <typename T, int N, int W, int KK = (N - 1) / 3, bool SHIFT = false>
 __global__ void __launch_bounds__(StridedCfg<T, N, W>::THREADS, StridedCfg<T, N, W>::MINB)
-k_zfwd(PassArgs a) {
+k_yfwd(PassArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  b_yfwd<T, N, W, KK, SHIFT>(a, hw_ctx(smraw));
+}
+
+template <typename T, int N, int W, int KK = (N - 1) / 3, bool SHIFT = false>
+__device__ __forceinline__ void b_zfwd(const PassArgs& a, const Tctx& tcx) {
   using C = typename CT<T>::type;
   constexpr int K = KK, M = KK + 1, P = 2 * KK + 1;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  unsigned char* smraw = tcx.smem;
   C* sm = reinterpret_cast<C*>(smraw);
-  const int w = threadIdx.x, t = threadIdx.y;
-  const int ix = blockIdx.x * W + w;
-  const int iy = blockIdx.y;
+  const int w = tcx.tx, t = tcx.ty;
+  const int ix = tcx.bx * W + w;
+  const int iy = tcx.by;
   const bool act = ix < M;
-  const C* __restrict__ yf = static_cast<const C*>(a.yf);
-  C* __restrict__ rb = static_cast<C*>(a.rb);
-  const C* tw = strided_twiddles<T, N, W>(smraw, static_cast<const C*>(a.tw));
+  const C* PSC_RESTRICT yf = static_cast<const C*>(a.yf);
+  C* PSC_RESTRICT rb = static_cast<C*>(a.rb);
+  const C* tw = strided_twiddles<T, N, W>(smraw, static_cast<const C*>(a.tw), tcx);
   const long long S = (long long)P * P * M, zs = (long long)N * P * M;
   const C zero = mk(T(0), T(0));
 #pragma unroll 1
@@ -389,6 +407,13 @@ k_zfwd(PassArgs a) {
         },
         sm, tw, t, w);
   }
+}
+
+template <typename T, int N, int W, int KK = (N - 1) / 3, bool SHIFT = false>
+__global__ void __launch_bounds__(StridedCfg<T, N, W>::THREADS, StridedCfg<T, N, W>::MINB)
+k_zfwd(PassArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  b_zfwd<T, N, W, KK, SHIFT>(a, hw_ctx(smraw));
 }
 
 // ---------------------------------------------------------------------------
@@ -529,25 +554,24 @@ __device__ __forceinline__ void umax_update(Ctrl* c, double v) {
 }
 
 template <typename T, int N, int MODE, int KK = (N - 1) / 3, bool SHIFT = false>
-__global__ void __launch_bounds__(32 * XCfg<T, N>::WARPS)
-k_xpass(PassArgs a) {
+__device__ __forceinline__ void b_xpass(const PassArgs& a, const Tctx& tcx) {
   using C = typename CT<T>::type;
   using PL = PlanD<N>;
   using XC = XCfg<T, N>;
   constexpr int R1 = PL::R1, R2 = PL::R2, TPL = PL::TPL, J2 = PL::J2, M = KK + 1;
   constexpr int LPW = XC::LPW;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned char* smraw = tcx.smem;
+  const int lane = tcx.tx & 31, wid = tcx.tx >> 5;
   const int t = lane % TPL, g = lane / TPL;
   unsigned char* myline = smraw + (size_t)(wid * LPW + g) * XC::LINE_BYTES;
   C* ex = reinterpret_cast<C*>(myline);
   T* stash = reinterpret_cast<T*>(myline + XC::EXCH * sizeof(C));
-  const C* __restrict__ yb = static_cast<const C*>(a.yb);
-  C* __restrict__ xb = static_cast<C*>(a.xb);
+  const C* PSC_RESTRICT yb = static_cast<const C*>(a.yb);
+  C* PSC_RESTRICT xb = static_cast<C*>(a.xb);
   C* tw = reinterpret_cast<C*>(smraw + XC::LINE_BYTES * LPW * XC::WARPS);
   {
-    const C* __restrict__ twg = static_cast<const C*>(a.tw);
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const C* PSC_RESTRICT twg = static_cast<const C*>(a.tw);
+    for (int i = tcx.tx; i < N; i += tcx.bdx) {
       const int tt = i % TPL;
       const int k1i = (i / TPL) % R1, ji = i / (TPL * R1);  // inverse: k1 < R1, j < J1
       tw[i] = twg[(tt + ji * TPL) * k1i];
@@ -564,8 +588,8 @@ k_xpass(PassArgs a) {
   MomentSum<T> acc[MODE == XMODE_STATS ? NQ : 1];
 
 #pragma unroll 1
-  for (long long grp = (long long)blockIdx.x * XC::WARPS + wid; grp * LPW < nlines;
-       grp += (long long)gridDim.x * XC::WARPS) {
+  for (long long grp = (long long)tcx.bx * XC::WARPS + wid; grp * LPW < nlines;
+       grp += (long long)tcx.gdx * XC::WARPS) {
     const long long line = grp * LPW + g;
     const bool valid = line < nlines;
     auto Y = [&](int s, int kx) -> C {
@@ -881,7 +905,7 @@ k_xpass(PassArgs a) {
     if (lane == 0) umax_update(a.ctrl, umax);
   }
   if constexpr (MODE == XMODE_STATS) {
-    const long long gw = (long long)blockIdx.x * XC::WARPS + wid;
+    const long long gw = (long long)tcx.bx * XC::WARPS + wid;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       double v = acc[q].value();
@@ -889,6 +913,13 @@ k_xpass(PassArgs a) {
       if (lane == 0) a.partials[gw * NQ + q] = v;
     }
   }
+}
+
+template <typename T, int N, int MODE, int KK = (N - 1) / 3, bool SHIFT = false>
+__global__ void __launch_bounds__(32 * XCfg<T, N>::WARPS)
+k_xpass(PassArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  b_xpass<T, N, MODE, KK, SHIFT>(a, hw_ctx(smraw));
 }
 
 }  // namespace psc

@@ -3,9 +3,16 @@
 Requests (grid size N, steps, viscosity, Schmidt number, seed) arrive over time.
 The server admits them in arrival order while their workspaces fit an HBM
 budget, keeps every admitted run's spectral state resident, steps all active
-runs together (one captured CUDA graph per RK4 step of the whole active set,
-rebuilt when the set changes), streams each run's statistics records, and
-retires runs as they finish, freeing their memory for waiting requests.
+runs together, streams each run's statistics records, and retires runs as
+they finish, freeing their memory for waiting requests.
+
+Two ways of stepping the active set: "persistent" (the default where every
+run qualifies: FP32-mixed at a persistent size) steps it with one persistent
+launch per RK stage over a device work table that is rewritten when runs join
+or leave, so nothing is recaptured; "graph" captures every member's kernels
+into one CUDA graph per RK4 step, rebuilt when the set changes.  While a
+chunk of steps runs on the GPU the host admits and initialises newly arrived
+runs.
 
 Everything numeric happens in libpsc's kernels; this module only schedules.
 """
@@ -85,10 +92,16 @@ class Server:
     stream of records a server returns); "final" only of each run when it ends."""
 
     def __init__(self, budget_bytes: float = 150e9, chunk: int = 50, device="cuda:0",
-                 clock=time.perf_counter, sleep=time.sleep, records: str = "chunk"):
+                 clock=time.perf_counter, sleep=time.sleep, records: str = "chunk", mode: str = "auto",
+                 max_boxes: int = 1024, max_N: int | None = None):
         if records not in ("chunk", "final"):
             raise ValueError("records must be 'chunk' or 'final'")
+        if mode not in ("auto", "persistent", "graph"):
+            raise ValueError("mode must be 'auto', 'persistent' or 'graph'")
         self.records = records
+        self.mode = mode
+        self.max_boxes = max_boxes
+        self.max_N = max_N
         import torch
         self.torch = torch
         self.budget = budget_bytes
@@ -98,20 +111,37 @@ class Server:
         self.sleep = sleep
         self.stream = torch.cuda.Stream(self.device)
 
+    def _persistent_ok(self, requests) -> bool:
+        return all(r.precision == B.FP32_MIXED and r.N in B.PERSISTENT_SIZES for r in requests)
+
     def run(self, requests, on_record=None):
         torch = self.torch
         pending = sorted(requests, key=lambda r: r.arrival)
+        mode = self.mode
+        if mode == "auto":
+            mode = "persistent" if self._persistent_ok(pending) else "graph"
+        elif mode == "persistent" and not self._persistent_ok(pending):
+            raise ValueError("persistent mode needs FP32-mixed runs at persistent sizes")
         active = []       # dicts: req, sim, left, records, admitted
         results = []
         used = 0
         batch = None
         dirty = True
+        stats = dict(mode=mode, graph_builds=0, graph_build_s=0.0, table_updates=0, chunks=0,
+                     grid_point_stages=0.0, peak_active=0, peak_bytes=0, records=0, step_s=0.0,
+                     admit_s=0.0, record_s=0.0)
+        if mode == "persistent":
+            max_N = self.max_N or max(r.N for r in pending)
+            max_N = min(n for n in B.PERSISTENT_SIZES if n >= max_N)
+            batch = B.PersistentBatch([], max_boxes=self.max_boxes, max_N=max_N, device=self.device,
+                                      stream=self.stream)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
         t0 = self.clock()
-        stats = dict(graph_builds=0, graph_build_s=0.0, chunks=0, grid_point_stages=0.0, peak_active=0,
-                     peak_bytes=0, records=0)
-        while pending or active:
-            now = self.clock() - t0
-            # admission: arrival order, while the next run's workspace fits the budget
+
+        def admit(now):
+            nonlocal used, dirty
+            ta = self.clock()
             while pending and pending[0].arrival <= now:
                 r = pending[0]
                 p = make_params(r)
@@ -123,28 +153,48 @@ class Server:
                 pending.pop(0)
                 sim = B.Simulation(p, device=self.device, stream=torch.cuda.Stream(self.device))
                 sim.init_field()
-                active.append(dict(req=r, sim=sim, left=r.steps, records=[], admitted=now, bytes=need))
+                active.append(dict(req=r, sim=sim, left=r.steps, records=[], admitted=now, bytes=need,
+                                   joined=False))
                 used += need
                 dirty = True
+            stats["admit_s"] += self.clock() - ta
+
+        while pending or active:
+            admit(self.clock() - t0)
             stats["peak_active"] = max(stats["peak_active"], len(active))
             stats["peak_bytes"] = max(stats["peak_bytes"], used)
             if not active:
+                now = self.clock() - t0
                 self.sleep(max(0.0, min(0.05, pending[0].arrival - now)))
                 continue
+            members = [a for a in active if a["left"] > 0]
             if dirty:
                 tb = self.clock()
-                if batch is not None:
-                    batch.close()
-                batch = B.Batch([a["sim"] for a in active], stream=self.stream)
-                stats["graph_builds"] += 1
+                if mode == "persistent":
+                    batch.set_members([a["sim"] for a in members])
+                    stats["table_updates"] += 1
+                else:
+                    if batch is not None:
+                        batch.close()
+                    batch = B.Batch([a["sim"] for a in members], stream=self.stream)
+                    stats["graph_builds"] += 1
                 stats["graph_build_s"] += self.clock() - tb
+                for a in members:
+                    a["joined"] = True
                 dirty = False
-            n = min(self.chunk, min(a["left"] for a in active))
+            n = min(self.chunk, min(a["left"] for a in members))
+            ev0.record(self.stream)
             batch.step(n)
+            ev1.record(self.stream)
+            # while the chunk runs: admit and initialise runs that have arrived
+            # (they join at the next chunk)
+            admit(self.clock() - t0)
             batch.synchronize()
+            stats["step_s"] += ev0.elapsed_time(ev1) / 1000.0
             stats["chunks"] += 1
             finished = []
-            for a in active:
+            tr = self.clock()
+            for a in members:
                 a["left"] -= n
                 stats["grid_point_stages"] += 4.0 * n * a["req"].N ** 3
                 if self.records == "chunk" or a["left"] == 0:
@@ -156,9 +206,15 @@ class Server:
                         on_record(a["req"].rid, rec)
                 if a["left"] == 0:
                     finished.append(a)
+            stats["record_s"] += self.clock() - tr
             if finished:
                 done_t = self.clock() - t0
-                if batch is not None:  # the graph refers to the members' memory
+                # the batch refers to the members' memory: drop them from it first
+                remaining = [a for a in active if a not in finished]
+                if mode == "persistent":
+                    batch.set_members([a["sim"] for a in remaining if a["joined"]])
+                    stats["table_updates"] += 1
+                elif batch is not None:
                     batch.close()
                     batch = None
                 for a in finished:
@@ -175,9 +231,12 @@ class Server:
             batch.close()
         wall = self.clock() - t0
         lat = np.array([r.latency for r in results])
+        idle = max(0.0, wall - stats["step_s"] - stats["record_s"] - stats["admit_s"] - stats["graph_build_s"])
         summary = dict(requests=len(results), wall_s=wall,
                        p50_latency_s=float(np.percentile(lat, 50)) if len(lat) else math.nan,
                        p99_latency_s=float(np.percentile(lat, 99)) if len(lat) else math.nan,
                        grid_point_stages_per_s=stats["grid_point_stages"] / wall if wall > 0 else math.nan,
-                       sims_per_hour=3600.0 * len(results) / wall if wall > 0 else math.nan, **stats)
+                       sims_per_hour=3600.0 * len(results) / wall if wall > 0 else math.nan,
+                       step_busy_fraction=stats["step_s"] / wall if wall > 0 else math.nan,
+                       other_s=idle, **stats)
         return sorted(results, key=lambda r: r.rid), summary
