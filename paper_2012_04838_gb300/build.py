@@ -79,8 +79,9 @@ def build(checked: bool | None = None, jobs: int | None = None, verbose: bool = 
     # the persistent ensemble kernel, one unit per RK stage
     for stage in (1, 2, 3, 4):
         obj = os.path.join(odir, f"batch_stage_{stage}.o")
-        units.append((obj, [cc] + flags + [f"-DPSCB_STAGE={stage}", "-c", os.path.join(CSRC, "psc_batch_stage.cu"),
-                                           "-o", obj]))
+        # global loads cached in L2 only: CTAs of one launch read what others wrote
+        units.append((obj, [cc] + flags + [f"-DPSCB_STAGE={stage}", "-Xptxas", "-dlcm=cg", "-c",
+                                           os.path.join(CSRC, "psc_batch_stage.cu"), "-o", obj]))
     todo = [(o, c) for o, c in units if not os.path.exists(o)]
     if todo:
         jobs = jobs or max(1, os.cpu_count() or 1)

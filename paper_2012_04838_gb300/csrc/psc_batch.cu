@@ -57,12 +57,14 @@ cudaError_t pscb_upload(void* table, void* staging, int max_boxes, const PscBatc
         s.box = bi;
         s.pass = p;
         s.tiles = t;
+        s.per = tiles_per_item(p);
+        const int items = (t + s.per - 1) / s.per;
         s.dep = last[bi];
         s.dep_tiles = last_tiles[bi];
         s.done_idx = bi * BP_N + p;
         last[bi] = s.done_idx;
-        last_tiles[bi] = t;
-        off += t;
+        last_tiles[bi] = items;  // done[] counts items
+        off += items;
       }
     }
     hd->nseg[stage - 1] = ns;

@@ -44,6 +44,7 @@ constexpr int kXGroupsPerWarp = 2;    // row groups per warp of an X-pass item
 struct Seg {
   long long start;  // index of the segment's first item within the stage
   int box, pass, tiles;
+  int per;          // tiles of the pass each item runs
   int dep;          // index into done[] of the pass this one waits for (-1: none)
   int dep_tiles;    // tiles that pass has
   int done_idx;     // index into done[] this segment counts into
@@ -107,6 +108,18 @@ template <int N> int tiles_of(int pass, int stage, const PscBatchBox& b) {
       return (int)((S + per - 1) / per);
     }
     default: return (stage == 4 && b.forcing == 2) ? 1 : 0;
+  }
+}
+
+// Tiles one work item runs: several small tiles per item keep the per-item
+// cost (taking an item, its dependency check, the completion count) small
+// against the work.
+inline int tiles_per_item(int pass) {
+  switch (pass) {
+    case BP_ZINV: case BP_YINV: case BP_YFWD: case BP_ZFWD: return 4;
+    case BP_XPASS: return 2;
+    case BP_COMBINE: return 4;
+    default: return 1;
   }
 }
 
@@ -237,8 +250,11 @@ constexpr unsigned long long kWaitNs = 2000000000ull;
 // The bound under the stall test (a dependency that is never met, see pscb_upload).
 constexpr unsigned long long kStallTestWaitNs = 50000000ull;
 
+#ifndef PSCB_MINB
+#define PSCB_MINB 3  // CTAs per SM the register budget is sized for
+#endif
 template <int STAGE, bool BIG>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, PSCB_MINB)
 k_batch_stage(const Head* head, const PscBatchBox* boxes, const Seg* segs, unsigned char* counters) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_seg, s_tile;
@@ -282,12 +298,17 @@ k_batch_stage(const Head* head, const PscBatchBox* boxes, const Seg* segs, unsig
       s_tile = tile;
     }
     __syncthreads();
-    const int sg = s_seg, tile = s_tile;
+    const int sg = s_seg, item = s_tile;
     if (sg < 0) break;
-    // every thread orders its reads after the producers' writes
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    // The producers' writes are ordered before thread 0's acquire, and the
+    // barrier orders that before every thread's reads.  This unit is built
+    // with global loads cached in L2 only (-dlcm=cg), so no SM keeps a stale
+    // L1 copy of a buffer another CTA has since rewritten.
     const Seg& g = segs[sg];
-    dispatch<STAGE, BIG>(boxes[g.box], g.pass, tile, g.tiles, tid, smraw);
+    for (int t = item * g.per; t < (item + 1) * g.per && t < g.tiles; ++t) {
+      dispatch<STAGE, BIG>(boxes[g.box], g.pass, t, g.tiles, tid, smraw);
+      if (g.per > 1) __syncthreads();  // bodies reuse the shared memory
+    }
     __syncthreads();
     if (tid == 0) {
       __threadfence();

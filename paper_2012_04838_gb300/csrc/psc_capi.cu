@@ -714,11 +714,12 @@ psc_status do_stats(psc_sim* s, double* Ek, double* Ephi, int cap, int* nshell, 
     r.P_inj = 2.0 * c.A * c.Ef;
   }
   (void)Vp;
-  if ((c.err & 2) || !(umax <= 1.7976931348623157e308))
-    return fail(PSC_EUNSTABLE, "non-finite velocity in the CFL monitor");
+  // a wait that gave up left the state incomplete: report it before what followed from it
   if (c.err & 4)
     return fail(PSC_ETIMEOUT, "a bounded device wait gave up (an asynchronous copy into shared memory, or a "
                               "dependency of the persistent ensemble kernel, did not complete in time)");
+  if ((c.err & 2) || !(umax <= 1.7976931348623157e308))
+    return fail(PSC_EUNSTABLE, "non-finite velocity in the CFL monitor");
   return PSC_OK;
 }
 

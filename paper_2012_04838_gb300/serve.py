@@ -6,13 +6,14 @@ budget, keeps every admitted run's spectral state resident, steps all active
 runs together, streams each run's statistics records, and retires runs as
 they finish, freeing their memory for waiting requests.
 
-Two ways of stepping the active set: "persistent" (the default where every
-run qualifies: FP32-mixed at a persistent size) steps it with one persistent
-launch per RK stage over a device work table that is rewritten when runs join
-or leave, so nothing is recaptured; "graph" captures every member's kernels
-into one CUDA graph per RK4 step, rebuilt when the set changes.  While a
-chunk of steps runs on the GPU the host admits and initialises newly arrived
-runs.
+Two ways of stepping the active set: "graph" (the default) captures every
+member's kernels into one CUDA graph per RK4 step, rebuilt when the set
+changes; "persistent" steps it with one persistent launch per RK stage over a
+device work table that is rewritten when runs join or leave, so nothing is
+recaptured (FP32-mixed runs at the persistent sizes; on GB300 it has run at
+about half the graph path's rate, its pass bodies being latency-bound at the
+occupancy one kernel for every pass allows).  While a chunk of steps runs on
+the GPU the host admits and initialises newly arrived runs.
 
 Everything numeric happens in libpsc's kernels; this module only schedules.
 """
@@ -92,12 +93,12 @@ class Server:
     stream of records a server returns); "final" only of each run when it ends."""
 
     def __init__(self, budget_bytes: float = 150e9, chunk: int = 50, device="cuda:0",
-                 clock=time.perf_counter, sleep=time.sleep, records: str = "chunk", mode: str = "auto",
+                 clock=time.perf_counter, sleep=time.sleep, records: str = "chunk", mode: str = "graph",
                  max_boxes: int = 1024, max_N: int | None = None):
         if records not in ("chunk", "final"):
             raise ValueError("records must be 'chunk' or 'final'")
-        if mode not in ("auto", "persistent", "graph"):
-            raise ValueError("mode must be 'auto', 'persistent' or 'graph'")
+        if mode not in ("graph", "persistent"):
+            raise ValueError("mode must be 'graph' or 'persistent'")
         self.records = records
         self.mode = mode
         self.max_boxes = max_boxes
@@ -118,9 +119,7 @@ class Server:
         torch = self.torch
         pending = sorted(requests, key=lambda r: r.arrival)
         mode = self.mode
-        if mode == "auto":
-            mode = "persistent" if self._persistent_ok(pending) else "graph"
-        elif mode == "persistent" and not self._persistent_ok(pending):
+        if mode == "persistent" and not self._persistent_ok(pending):
             raise ValueError("persistent mode needs FP32-mixed runs at persistent sizes")
         active = []       # dicts: req, sim, left, records, admitted
         results = []
