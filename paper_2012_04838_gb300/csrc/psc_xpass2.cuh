@@ -68,11 +68,15 @@ template <int G> __device__ __forceinline__ int bitrev_lane(int r) {
 template <typename T, int G, int DIR>
 __device__ __forceinline__ void lane_dft(typename CT<T>::type (&v)[16], int r) {
   using C = typename CT<T>::type;
+  // the upper lane of a pair forms o - v, the lower v + o: one fused
+  // multiply-add by a per-lane sign, fma(-1, v, o) = o - v and fma(1, v, o) =
+  // v + o exactly, instead of both sums and a select
   auto bfly = [&](int mask, bool upper) {
+    const T sg = upper ? T(-1) : T(1);
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       const C o = mk(__shfl_xor_sync(0xffffffffu, v[i].x, mask), __shfl_xor_sync(0xffffffffu, v[i].y, mask));
-      v[i] = upper ? csub(o, v[i]) : cadd(v[i], o);
+      v[i] = mk(fma(sg, v[i].x, o.x), fma(sg, v[i].y, o.y));
     }
   };
   auto quarter = [&]() {  // multiply by exp(DIR * 2 pi i / 4) on the lane with both bits set
@@ -93,6 +97,30 @@ __device__ __forceinline__ void lane_dft(typename CT<T>::type (&v)[16], int r) {
     bfly(2, r & 2);
   }
 }
+
+// The first DFT-16 of an inverse transform: slots m whose 16 G positions all
+// lie in the zero band for every thread (band_of_k == 0) are known zeros, and
+// the pruned codelet DftZ<16, +1, Z0, Z1> skips them (the generator emits it
+// for slots 6..9, the band of the 2/3 rule at N = 512 and 1024); a plain
+// DFT-16 otherwise.  Adding a known zero is left out, so the sums are the same.
+template <int N, int KK> struct x2_first_inverse {
+  static constexpr int TH = X2Cfg<float, N>::TH;
+  static constexpr int first() {
+    for (int m = 0; m < 16; ++m)
+      if (band_of_k(N, TH, m, KK) == 0) return m;
+    return 16;
+  }
+  static constexpr int last() {
+    for (int m = 15; m >= 0; --m)
+      if (band_of_k(N, TH, m, KK) == 0) return m;
+    return -1;
+  }
+  static constexpr bool PRUNED = first() == 6 && last() == 9;
+  template <typename T, typename C> static __device__ __forceinline__ void run(C (&v)[16]) {
+    if constexpr (PRUNED) DftZ<16, +1, 6, 9>::template run<T, C>(v);
+    else Dft<16, +1>::template run<T, C>(v);
+  }
+};
 
 template <typename C> struct X2Roles {
   int tid;  // thread within the row: inverse input / forward output column j
@@ -154,7 +182,7 @@ __device__ __forceinline__ void x2inv(const SPEC& spec, typename CT<T>::type (&z
       }
     }
   });
-  Dft<16, +1>::template run<T, C>(v);  // over k2 -> a
+  x2_first_inverse<N, KK>::template run<T, C>(v);  // over k2 -> a
 #pragma unroll
   for (int a = 0; a < 16; ++a) {
     C w = v[a];
