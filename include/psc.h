@@ -324,11 +324,12 @@ psc_status psc_xpass_probe(int32_t N, int32_t precision, int64_t rows, void* buf
                            int32_t nlaunch);
 
 /* Measurement aid (no counterpart in the paper): `blocks` CTAs of 256 threads
- * each run 8 independent chains of 128 * iters fused multiply-adds in FP32
- * (PSC_FP32_MIXED) or FP64, storing one value per thread to the device buffer
- * `out` (blocks * 256 elements).  2 * 8 * 128 * iters * 256 * blocks floating-
- * point operations; timed by the caller, it gives the device's FMA peak that
- * the FP32 and FP64 paths are compared against.  Asynchronous on `stream`. */
+ * whose threads each run 128 * iters fused multiply-adds (8 independent chains
+ * of 16 * iters) in FP32 (PSC_FP32_MIXED) or FP64, storing one value per
+ * thread to the device buffer `out` (blocks * 256 elements).  That is
+ * 2 * 128 * iters * 256 * blocks floating-point operations; timed by the
+ * caller, it gives the device's FMA peak that the FP32 and FP64 paths are
+ * compared against.  Asynchronous on `stream`. */
 psc_status psc_fma_probe(int32_t precision, int32_t iters, int32_t blocks, void* out, void* stream);
 
 /* Message for the last failing call on this thread (never NULL). */

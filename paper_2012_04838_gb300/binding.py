@@ -462,5 +462,5 @@ def fma_peak_tflops(precision: int, device=None, iters: int = 2000, repeats: int
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1)
         best = ms if best is None else min(best, ms)
-    flops = 2.0 * 8 * 128 * iters * 256 * blocks
+    flops = 2.0 * 128 * iters * 256 * blocks  # 128 iters FMAs per thread
     return flops / (best / 1000.0) / 1e12
