@@ -107,7 +107,13 @@ typedef struct {
 /* One statistics record of the current state (section 2.3): Table 1,
  * Eqs. 11-12 (velocity- and scalar-gradient skewness and flatness) and the
  * terms of Eq. 13.  eps and chi come from the spectrum; eps_phys = nu <|omega|^2>
- * and chi_phys = 2 D <|grad phi|^2> are grid averages (equal up to rounding). */
+ * and chi_phys = 2 D <|grad phi|^2> are grid averages (equal up to rounding).
+ * Precision: every sum is finished in FP64 in a fixed order.  With
+ * PSC_FP32_MIXED each thread first accumulates its share in compensated FP32
+ * (the shell sums behind E(n), K, eps, chi, phi_var, phi_prod, E_forced; the
+ * grid moments behind K_phys, eps_phys, chi_phys, phi_prod_phys, skew, flat,
+ * skew_phi, flat_phi), which keeps these fields within 2e-5 relative of the
+ * FP64 values (skewness and flatness within 1e-4 absolute; tested). */
 typedef struct {
   double t, dt;
   double K, K_phys, eps, eps_phys, eta, Re_lambda, Te, urms, lambda, l0;
