@@ -166,6 +166,7 @@ struct psc_sim {
   int nshell;
   int wv[SP_N];  // tile-width variant of each strided pass (autotuned at creation)
   int xrow = 0;  // PSC_XPASS_ROWS=1 at creation: the row X pass where the register one exists
+  int stall_test = 0;  // PSC_XPASS_STALL_TEST=1 at creation: failure-path test of the TMA waits
   // launch accounting and optional per-launch event timing
   int64_t launches = 0;
   bool profiling = false;
@@ -288,6 +289,10 @@ psc_status psc_create(const psc_params* p, void* dev_ws, size_t ws_bytes, void* 
     // test knob: the shared-memory row X pass at sizes that also have the register one
     const char* xr = std::getenv("PSC_XPASS_ROWS");
     sim->xrow = (xr && xr[0] == '1') ? 1 : 0;
+    // test knob: the X pass's first staged row never completes and its waits are
+    // bounded at 1 ms, so the failure path (PSC_ETIMEOUT) runs without a fault
+    const char* st = std::getenv("PSC_XPASS_STALL_TEST");
+    sim->stall_test = (st && st[0] == '1') ? 1 : 0;
   }
   // twiddles, control block, zero state
   const int N = p->N;
@@ -299,6 +304,8 @@ psc_status psc_create(const psc_params* p, void* dev_ws, size_t ws_bytes, void* 
   std::memset(&c0, 0, sizeof(c0));
   c0.dt = p->dt;
   c0.Ef0 = -1.0;
+  c0.stall_test = sim->stall_test;
+  c0.wait_ns = sim->stall_test ? 1000000ull : 0ull;
   cudaError_t e;
   if (sim->fp64) e = cudaMemcpyAsync(sim->ws + L.tw, twd.data(), twd.size() * 8, cudaMemcpyHostToDevice, sim->st);
   else e = cudaMemcpyAsync(sim->ws + L.tw, twf.data(), twf.size() * 4, cudaMemcpyHostToDevice, sim->st);
@@ -620,6 +627,8 @@ psc_status do_init(psc_sim* s) {
   std::memset(&c0, 0, sizeof(c0));
   c0.dt = s->p.dt;
   c0.Ef0 = -1.0;
+  c0.stall_test = s->stall_test;
+  c0.wait_ns = s->stall_test ? 1000000ull : 0ull;
   PSC_CUDA(cudaMemcpyAsync(s->ctrl, &c0, sizeof(c0), cudaMemcpyHostToDevice, s->st));
   launch_iftab<T>(s);
   PSC_LAUNCHED("psc_init_field");

@@ -187,18 +187,20 @@ __device__ __forceinline__ unsigned long long global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// wait for the phase of parity `parity` to complete; false once about two
-// seconds have passed (a time bound, whatever each poll's own suspend time),
-// or as soon as bit 2 of *abort is seen set (another wait already gave up)
+// wait for the phase of parity `parity` to complete; false once limit_ns
+// (about two seconds by default) have passed (a time bound, whatever each
+// poll's own suspend time), or as soon as bit 2 of *abort is seen set
+// (another wait already gave up)
 __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity,
-                                          const int* abort = nullptr) {
+                                          const int* abort = nullptr,
+                                          unsigned long long limit_ns = 2000000000ull) {
   if (mbar_try_wait(b, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (unsigned i = 1;; ++i) {
     if (mbar_try_wait(b, parity)) return true;
     if ((i & 255u) == 0) {
       if (abort && (*(const volatile int*)abort & 4)) return false;
-      if (global_ns() - t0 > 2000000000ull) return false;
+      if (global_ns() - t0 > limit_ns) return false;
     }
   }
 }

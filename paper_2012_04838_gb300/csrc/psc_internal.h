@@ -72,6 +72,9 @@ struct Ctrl {
   long long step;                 // RK4 steps taken (advanced by the last stage of each step)
   double Ef0;                     // band energy held by the deterministic forcing (< 0: not yet set)
   double Ef_start;                // band energy of the state at the start of the current step
+  unsigned long long wait_ns;     // bound of the TMA waits (0: two seconds)
+  int stall_test;                 // 1: the X pass's first staged row of CTA 0 never completes (test)
+  int pad2;
 };
 
 // Streams of the intermediate buffers (indices into zb / yb).

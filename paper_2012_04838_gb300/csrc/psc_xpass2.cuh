@@ -653,10 +653,16 @@ __global__ void __launch_bounds__(X2SCfg<T, N>::THREADS, 1) k_xpass2s(PassArgs a
   const long long stride = (long long)gridDim.x * ROWS;
   const T scale = T(1.0 / ((double)N * N * N));
   const bool leader = q.tid == 0;
+  // bound of the waits; the failure-path test asks one more transaction byte
+  // than the copies bring for the first row of CTA 0's first row group, so that
+  // row's wait runs out (every copy still lands)
+  const unsigned long long lim = a.ctrl->wait_ns ? a.ctrl->wait_ns : 2000000000ull;
+  bool stall = a.ctrl->stall_test != 0 && blockIdx.x == 0 && lid == 0;
   // copies of streams [s0, s1) of row ln into the staging slots (one thread)
   auto issue = [&](long long ln, int s0, int s1, unsigned long long* bar) {
     fence_proxy_async_smem();
-    mbar_expect_tx(bar, (unsigned)(s1 - s0) * SC::ROW_BYTES);
+    mbar_expect_tx(bar, (unsigned)(s1 - s0) * SC::ROW_BYTES + (stall ? 16u : 0u));
+    stall = false;
     for (int st = s0; st < s1; ++st) {
       const long long src = st * ys + ln * M;
       if (PSC_OK_INDEX(src + M - 1, (long long)Y_NSTREAM * ys, a.ctrl))
@@ -681,7 +687,7 @@ __global__ void __launch_bounds__(X2SCfg<T, N>::THREADS, 1) k_xpass2s(PassArgs a
     const long long next = line + stride;
     // the row's first thread polls; the row barrier shares the outcome and
     // makes the staged streams visible to the row's threads
-    ok = bar_and(q.bar, TH, leader ? mbar_wait(barA, pa, &a.ctrl->err) : true);
+    ok = bar_and(q.bar, TH, leader ? mbar_wait(barA, pa, &a.ctrl->err, lim) : true);
     if (!ok) break;
     pa ^= 1u;
     ia = false;
@@ -700,7 +706,7 @@ __global__ void __launch_bounds__(X2SCfg<T, N>::THREADS, 1) k_xpass2s(PassArgs a
         },
         [&] {
           if constexpr (!SC::STAGE_B) return true;
-          const bool w = bar_and(q.bar, TH, leader ? mbar_wait(barB, pb, &a.ctrl->err) : true);
+          const bool w = bar_and(q.bar, TH, leader ? mbar_wait(barB, pb, &a.ctrl->err, lim) : true);
           if (w) {
             pb ^= 1u;
             ib = false;
@@ -723,8 +729,8 @@ __global__ void __launch_bounds__(X2SCfg<T, N>::THREADS, 1) k_xpass2s(PassArgs a
     // a bounded time to land in this CTA's shared memory, and stop
     if (leader) {
       atomicOr(&a.ctrl->err, 4);
-      if (ia) mbar_wait(barA, pa);
-      if (ib) mbar_wait(barB, pb);
+      if (ia) mbar_wait(barA, pa, nullptr, lim);
+      if (ib) mbar_wait(barB, pb, nullptr, lim);
     }
   }
   if (a.want_umax) {

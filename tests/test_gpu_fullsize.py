@@ -172,3 +172,38 @@ def test_fullsize_steps_conserve_budget(sim):
     src = 0.5 * ((r0["P_inj"] - r0["eps"]) + (r1["P_inj"] - r1["eps"])) * dt
     assert abs(dK - src) < 0.05 * abs(r0["eps"]) * dt + 1e-6
     assert abs(r0["cfl"] - 0.5) < 1e-5
+
+
+def test_xpass_tma_wait_runs_out_and_reports_timeout(monkeypatch):
+    """The failure path of the X pass's bounded TMA waits, without a GPU fault:
+    with PSC_XPASS_STALL_TEST=1 at creation, CTA 0 asks its first staged row's
+    mbarrier for 16 transaction bytes more than its copies bring (every copy
+    still lands), so that wait runs out after 1 ms; the row group stops, the
+    simulation reports PSC_ETIMEOUT at its next statistics call, and a fresh
+    simulation afterwards steps and reports normally."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p = B.Params(N=N, precision=B.FP32_MIXED, nu=3.341e-4, Sc=1.0, beta=1.0, eps_inj=0.1, kF=2.0,
+                 dt=2e-4, ic=B.IC_SPECTRUM_K4, seed=5, ic_energy=1.5)
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    if free < B.workspace_size(p) + 16e9:
+        pytest.skip("not enough device memory for the 1024^3 case")
+    monkeypatch.setenv("PSC_XPASS_STALL_TEST", "1")
+    s = B.Simulation(p, device="cuda:0")
+    monkeypatch.delenv("PSC_XPASS_STALL_TEST")
+    s.init_field()
+    s.step(1)
+    with pytest.raises(B.PscError) as e:
+        s.stats()
+    assert e.value.status == B.PSC_ETIMEOUT
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    s = B.Simulation(p, device="cuda:0")
+    s.init_field()
+    s.step(1)
+    rec, _, _ = s.stats()
+    assert rec["step"] == 1 and rec["K"] > 0
+    s.close()
+    torch.cuda.empty_cache()
