@@ -21,7 +21,9 @@
  *   - Threads: one simulation must not be used from two host threads at once;
  *     distinct simulations are independent.
  *   - Spectral layout ("compact state"): with K = floor((N-1)/3) (2/3 rule;
- *     with PSC_DEALIAS_PHASE_SHIFT the largest k with 9 k^2 < 2 N^2),
+ *     with PSC_DEALIAS_PHASE_SHIFT the largest k with 9 k^2 < 2 N^2, or one
+ *     more where that makes K + 1 even and 2K + 1 <= N: the planes it adds lie
+ *     outside the sphere and are zero),
  *     P = 2K+1 and M = K+1, the state is four fields (u1, u2, u3, phi), each
  *     a [P][P][M] array of complex numbers (interleaved real, imaginary) with
  *     element [kz+K][ky+K][kx] holding the unnormalised Fourier coefficient
@@ -70,8 +72,8 @@ typedef enum { PSC_INTEG_IFRK4 = 0, PSC_INTEG_RK4 = 1 } psc_integrator;
 /* Dealiasing of the products (section 2.3).  TWO_THIRDS: the retained set is the
  * cube |k_i| <= K = (N-1)/3, whose quadratic products are alias-free on one grid.
  * PHASE_SHIFT: the paper's sphere |k| < sqrt(2) N / 3, stored in the cube of
- * half-width K = the largest k with 9 k^2 < 2 N^2 (modes of that cube outside the
- * sphere are zero); every product is formed on the grid and on the grid shifted
+ * half-width K of the layout above (modes of that cube outside the sphere are
+ * zero); every product is formed on the grid and on the grid shifted
  * by half a cell in each direction, and the two transforms are averaged, which
  * cancels the aliases that the sphere alone leaves (Patterson and Orszag 1971).
  * Twice the transforms of the right-hand side; psc_pressure is not offered with

@@ -178,14 +178,22 @@ def supported_sizes() -> list[int]:
     return list(buf[:n])
 
 
+def sphere_halfwidth(N: int) -> int:
+    """The largest k with 9 k^2 < 2 N^2 (the sphere of phase-shift dealiasing)."""
+    k = 0
+    while 9 * (k + 1) ** 2 < 2 * N * N:
+        k += 1
+    return k
+
+
 def retained_halfwidth(N: int, dealias: int = DEALIAS_TWO_THIRDS) -> int:
-    """K of the compact layout: (N-1)//3 (2/3 rule), or the largest k with
-    9 k^2 < 2 N^2 (the cube holding the sphere of phase-shift dealiasing)."""
+    """K of the compact layout: (N-1)//3 (2/3 rule), or the half-width of the
+    cube that stores the sphere of phase-shift dealiasing: the sphere's own, or
+    one more where that makes K + 1 even and the cube still fits the grid (the
+    added planes lie outside the sphere and stay zero)."""
     if dealias == DEALIAS_PHASE_SHIFT:
-        k = 0
-        while 9 * (k + 1) ** 2 < 2 * N * N:
-            k += 1
-        return k
+        k = sphere_halfwidth(N)
+        return k + 1 if k % 2 == 0 and 2 * (k + 1) + 1 <= N else k
     return (N - 1) // 3
 
 

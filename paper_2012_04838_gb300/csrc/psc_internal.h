@@ -35,12 +35,22 @@ __host__ __device__ constexpr int sphere_halfwidth(int N) {
   return k;
 }
 
-// Retained half-width K: the 2/3 rule (N-1)/3, or the sphere's half-width.
+// Half-width of the cube that stores the sphere: the sphere's own half-width,
+// or one more where that makes a kx row an even number of complex values (a
+// 16-byte multiple in FP32, which the tensor maps of the TMA-staged passes
+// need) and the cube still fits the grid.  The added planes lie outside the
+// sphere and stay zero.
+__host__ __device__ constexpr int sphere_storage_halfwidth(int N) {
+  return (sphere_halfwidth(N) % 2 == 0 && 2 * (sphere_halfwidth(N) + 1) + 1 <= N) ? sphere_halfwidth(N) + 1
+                                                                                    : sphere_halfwidth(N);
+}
+
+// Retained half-width K: the 2/3 rule (N-1)/3, or the cube that stores the sphere.
 inline Dims make_dims(int N, int sph = 0) {
   Dims d;
   d.N = N;
   d.sph = sph ? 1 : 0;
-  d.K = sph ? sphere_halfwidth(N) : (N - 1) / 3;
+  d.K = sph ? sphere_storage_halfwidth(N) : (N - 1) / 3;
   d.M = d.K + 1;
   d.P = 2 * d.K + 1;
   d.S = (long long)d.P * d.P * d.M;
@@ -51,9 +61,10 @@ inline Dims make_dims(int N, int sph = 0) {
 
 // Shells n = 0 .. floor(|k|_max + 1/2), n = floor(|k| + 1/2), of the retained
 // set: up to the cube's corner |k| = sqrt(3) K under the 2/3 rule; below
-// sqrt(2) N / 3 for the sphere (at most K + 1 there, so K + 2 shells).
+// sqrt(2) N / 3 for the sphere (at most its half-width + 1 there, so that + 2
+// shells).
 inline int shell_count(const Dims& d) {
-  if (d.sph) return d.K + 2;
+  if (d.sph) return sphere_halfwidth(d.N) + 2;
   // largest n with n^2 - n < 3 K^2 (the shell of the corner), in integers
   const long long k2 = 3LL * d.K * d.K;
   long long n = 0;

@@ -1028,7 +1028,9 @@ template <typename T, int N> struct Passes {
 #ifndef PSC_STAGED
 #define PSC_STAGED 1
 #endif
-  static constexpr bool STAGED = PSC_STAGED && sizeof(T) == 4 && N >= 64 && M % 2 == 0 && TPL >= 4;
+  // the plan and precision allow staged variants (the row length is the caller's)
+  static constexpr bool STAGED_OK = PSC_STAGED && sizeof(T) == 4 && N >= 64 && TPL >= 4;
+  static constexpr bool STAGED = STAGED_OK && M % 2 == 0;
   // variant 4: staged, 16 columns, for the inverse passes where it fits one CTA
   static constexpr bool STAGED16 = STAGED && StagedTile<T, N, 16, true>::SMEM <= 227 * 1024;
   static constexpr int NV = STAGED16 ? 5 : STAGED ? 4 : (WV0 != WV1 ? 2 : 1);
@@ -1195,7 +1197,7 @@ template <typename T, int N> struct Passes {
 // every direction (a.shift = 1: inputs times exp(i k pi/N) per axis, outputs
 // times its conjugate).
 template <typename T, int N> struct PassesPS {
-  static constexpr int KS = sphere_halfwidth(N);
+  static constexpr int KS = sphere_storage_halfwidth(N);
   static constexpr int TPL = PlanD<N>::TPL;
   static constexpr int M = KS + 1, P = 2 * KS + 1;
   static constexpr int WV0 = 8, WV1 = sizeof(T) == 4 ? 16 : 8;
@@ -1228,6 +1230,14 @@ template <typename T, int N> struct PassesPS {
       if (ROWS || a.xrow) return B::template xrow_launch<MODE, KS, SH>(a);
     }
     if constexpr (B::X2) {
+      if constexpr (B::X2S && MODE == XMODE_RHS) {
+        // the right-hand side at N = 1024 stages its rows through shared memory
+        using SC = X2SCfg<T, N, KS>;
+        const long long rows = (long long)N * N / SC::ROWS;
+        const int grid = (int)(rows < B::sm_count() ? rows : B::sm_count());
+        go(k_xpass2s<T, N, KS, SH>, dim3(grid), dim3(SC::THREADS), SC::SMEM, a);
+        return;
+      }
       go(k_xpass2<T, N, MODE, KS, SH>, dim3(B::xgrid()), dim3(128), X2Cfg<T, N>::SMEM, a);
     } else if constexpr (!ROWS) {
       go(k_xpass<T, N, MODE, KS, SH>, dim3(B::xgrid()), dim3(32 * XCfg<T, N>::WARPS), XCfg<T, N>::SMEM, a);
@@ -1245,13 +1255,81 @@ template <typename T, int N> struct PassesPS {
     else if (ym == YMODE_CONVECTIVE) a.shift ? yinv_k<W, YMODE_CONVECTIVE, true>(a) : yinv_k<W, YMODE_CONVECTIVE, false>(a);
     else a.shift ? yinv_k<W, YMODE_RHS, true>(a) : yinv_k<W, YMODE_RHS, false>(a);
   }
-  static void zinv(const PassArgs& a, bool stats, int v) { v == 1 ? zinv_w<WV1>(a, stats) : zinv_w<WV0>(a, stats); }
-  static void yinv(const PassArgs& a, int ym, int v) { v == 1 ? yinv_w<WV1>(a, ym) : yinv_w<WV0>(a, ym); }
+  // variants 2-4: input tiles staged by TMA (4, 8 and, for the inverse passes,
+  // 16 columns), where the stored cube's kx rows are 16-byte multiples
+  static constexpr bool STAGED = B::STAGED_OK && M % 2 == 0;
+  static constexpr bool STAGED16 = STAGED && StagedTile<T, N, 16, true, KS>::SMEM <= 227 * 1024;
+  static constexpr int NVS = STAGED16 ? 5 : STAGED ? 4 : NV;
+  static constexpr unsigned MASK_INV = (1u << NVS) - 1u;
+  static constexpr unsigned MASK_FWD = STAGED16 ? 0xFu : (1u << NVS) - 1u;
+  template <int W, int PASS, int MODE, bool SH> static bool launch_s(const PassArgs& a) {
+    if constexpr (STAGED) {
+      using TL = StagedTile<T, N, W, PASS == SP_ZINV || PASS == SP_YINV, KS>;
+      CUtensorMap m;
+      bool ok;
+      int rows;
+      if constexpr (PASS == SP_ZINV) {
+        ok = make_row_map(&m, a.in, 3, M, P, 4LL * P, (long long)P * M, W, TL::BOXR);
+        rows = P;
+      } else if constexpr (PASS == SP_YINV) {
+        ok = make_row_map(&m, a.zb, 2, M, (long long)Z_NSTREAM * N * P, 0, 0, W, TL::BOXR);
+        rows = N;
+      } else if constexpr (PASS == SP_YFWD) {
+        ok = make_row_map(&m, a.xb, 2, M, 4LL * N * N, 0, 0, W, TL::BOXR);
+        rows = N;
+      } else {
+        ok = make_row_map(&m, a.yf, 3, M, P, 4LL * N, (long long)P * M, W, TL::BOXR);
+        rows = P;
+      }
+      if (!ok) return false;
+      B::prep(k_strided_s<T, N, W, PASS, MODE, KS, SH>, TL::SMEM);
+      k_strided_s<T, N, W, PASS, MODE, KS, SH><<<dim3((M + W - 1) / W, rows), dim3(W, TPL), TL::SMEM, a.st>>>(a, m);
+      return true;
+    } else {
+      (void)a;
+      return false;
+    }
+  }
+  template <int PASS, int W, int MODE> static bool staged_sh(const PassArgs& a) {
+    return a.shift ? launch_s<W, PASS, MODE, true>(a) : launch_s<W, PASS, MODE, false>(a);
+  }
+  // mode: z-inverse 0/1 (right-hand side / 8 streams), y-inverse YMODE_*; the
+  // statistics stream sets run on the grid itself only
+  template <int PASS, int W> static bool staged_w(const PassArgs& a, int mode) {
+    if constexpr (PASS == SP_YINV) {
+      if (mode == YMODE_STATS) return launch_s<W, PASS, YMODE_STATS, false>(a);
+      if (mode == YMODE_CONVECTIVE) return staged_sh<PASS, W, YMODE_CONVECTIVE>(a);
+      return staged_sh<PASS, W, YMODE_RHS>(a);
+    } else if constexpr (PASS == SP_ZINV) {
+      return mode ? staged_sh<PASS, W, 1>(a) : staged_sh<PASS, W, 0>(a);
+    } else {
+      (void)mode;
+      return staged_sh<PASS, W, 0>(a);
+    }
+  }
+  template <int PASS> static bool staged(const PassArgs& a, int mode, int v) {
+    if (v == 2) return staged_w<PASS, 4>(a, mode);
+    if constexpr (STAGED16 && (PASS == SP_ZINV || PASS == SP_YINV)) {
+      if (v == 4) return staged_w<PASS, 16>(a, mode);
+    }
+    return staged_w<PASS, 8>(a, mode);
+  }
+  // a staged variant falls back to variant 0 if its tensor map cannot be made
+  static void zinv(const PassArgs& a, bool stats, int v) {
+    if (v >= 2 && staged<SP_ZINV>(a, stats ? 1 : 0, v)) return;
+    v == 1 ? zinv_w<WV1>(a, stats) : zinv_w<WV0>(a, stats);
+  }
+  static void yinv(const PassArgs& a, int ym, int v) {
+    if (v >= 2 && staged<SP_YINV>(a, ym, v)) return;
+    v == 1 ? yinv_w<WV1>(a, ym) : yinv_w<WV0>(a, ym);
+  }
   static void yfwd(const PassArgs& a, int v) {
+    if (v >= 2 && staged<SP_YFWD>(a, 0, v)) return;
     if (v == 1) a.shift ? yfwd_k<WV1, true>(a) : yfwd_k<WV1, false>(a);
     else a.shift ? yfwd_k<WV0, true>(a) : yfwd_k<WV0, false>(a);
   }
   static void zfwd(const PassArgs& a, int v) {
+    if (v >= 2 && staged<SP_ZFWD>(a, 0, v)) return;
     if (v == 1) a.shift ? zfwd_k<WV1, true>(a) : zfwd_k<WV1, false>(a);
     else a.shift ? zfwd_k<WV0, true>(a) : zfwd_k<WV0, false>(a);
   }
@@ -1263,11 +1341,10 @@ template <typename T, int N> struct PassesPS {
     a.shift ? xpass_k<XMODE_RHS, true>(a) : xpass_k<XMODE_RHS, false>(a);
   }
   static const PassTable* table() {
-    constexpr unsigned MASK = (1u << NV) - 1u;
     static const PassTable tb = {&zinv, &yinv, &xpass, &yfwd, &zfwd,
-                                 B::xwarps(), NV,
-                                 {WV0, WV1, WV1, WV1, WV1}, {0, 0, 0, 0, 0},
-                                 {MASK, MASK, MASK, MASK}, ROWS ? 1 : 0};
+                                 B::xwarps(), NVS,
+                                 {WV0, WV1, 4, 8, 16}, {0, 0, 1, 1, 1},
+                                 {MASK_INV, MASK_INV, MASK_FWD, MASK_FWD}, ROWS ? 1 : 0};
     return &tb;
   }
 };

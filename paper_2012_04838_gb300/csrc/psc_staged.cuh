@@ -35,11 +35,14 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, in
 // Staging tile of a pass: ROWS line positions (the P retained wavenumbers of an
 // inverse pass, the N points of a forward pass) of W complex values each,
 // fetched as NBOX boxes of BOXR rows (a box has at most 256 rows).
-template <typename T, int N, int W, bool INV> struct StagedTile {
+template <typename T, int N, int W, bool INV, int KK = (N - 1) / 3> struct StagedTile {
   using C = typename CT<T>::type;
-  static constexpr int ROWS = INV ? PlanD<N>::P : N;
+  static constexpr int ROWS = INV ? 2 * KK + 1 : N;
   static constexpr int NBOX = (ROWS + 255) / 256;
-  static constexpr int BOXR = (((ROWS + NBOX - 1) / NBOX) + 1) & ~1;
+  // rows per box: enough for NBOX boxes to cover ROWS, rounded up so that every
+  // box starts 128-byte aligned (a multiple of 128 / (W * sizeof(C)) rows, and even)
+  static constexpr int RALIGN = 128 / (W * (int)sizeof(C)) > 2 ? 128 / (W * (int)sizeof(C)) : 2;
+  static constexpr int BOXR = ((ROWS + NBOX - 1) / NBOX + RALIGN - 1) / RALIGN * RALIGN;
   static constexpr unsigned BOX_BYTES = (unsigned)(BOXR * W * sizeof(C));
   static constexpr unsigned BYTES = NBOX * BOX_BYTES;
   // The exchange buffer, then the staging tile, then (TW_SMEM) the step-1
@@ -71,7 +74,7 @@ template <typename T, int N, int W, bool INV> struct StagedTile {
 // strided_twiddles (TW_SMEM) or from the global table tw.  It does not end
 // with a barrier: the caller's next CTA barrier must come before the exchange
 // buffer is written again.
-template <typename T, int N, int W, int DIR, bool TW_SMEM, class ST>
+template <typename T, int N, int W, int DIR, bool TW_SMEM, int KK, class ST>
 __device__ __forceinline__ void strided_fft_regs(typename CT<T>::type (&in)[PlanD<N>::J1][PlanD<N>::R1],
                                                  const ST& st, typename CT<T>::type* sm,
                                                  const typename CT<T>::type* __restrict__ tw, int t, int w) {
@@ -82,7 +85,7 @@ __device__ __forceinline__ void strided_fft_regs(typename CT<T>::type (&in)[Plan
 #pragma unroll
   for (int j = 0; j < J1; ++j) {
     const int n2 = t + j * TPL;
-    first_dft<T, N, DIR>(in[j]);
+    first_dft<T, N, DIR, KK>(in[j]);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       C v = in[j][k1];
@@ -104,7 +107,7 @@ __device__ __forceinline__ void strided_fft_regs(typename CT<T>::type (&in)[Plan
     Dft<R2, DIR>::template run<T, C>(b);
     static_for<0, R2>([&](auto kc) {
       constexpr int k2 = decltype(kc)::value;
-      if constexpr (!(DIR < 0 && dead_k2<N>(k2))) st(k1 + R1 * k2, b[k2]);
+      if constexpr (!(DIR < 0 && dead_k2<N, KK>(k2))) st(k1 + R1 * k2, b[k2]);
     });
   }
 }
@@ -161,16 +164,19 @@ template <int PASS, int MODE> struct StagedPlan {
 //   y-inverse: z-stage streams, 2D {2M, Z_NSTREAM N P}
 //   y-forward: x-pass output,   2D {2M, 4 N N}
 //   z-forward: y-forward output, 3D {2M, P (ky), 4N (stream, z)}
-template <typename T, int N, int W, int PASS, int MODE>
+// KK: the retained half-width (the 2/3 rule's, or the cube that stores the
+// phase-shift sphere); SHIFT: the inputs are multiplied by exp(i k pi / N) and
+// the outputs by its conjugate (the grid shifted by half a cell).
+template <typename T, int N, int W, int PASS, int MODE, int KK = (N - 1) / 3, bool SHIFT = false>
 __global__ void __launch_bounds__(W * PlanD<N>::TPL,
-                                  StagedTile<T, N, W, PASS == SP_ZINV || PASS == SP_YINV>::MINB)
+                                  StagedTile<T, N, W, PASS == SP_ZINV || PASS == SP_YINV, KK>::MINB)
 k_strided_s(PassArgs a, const __grid_constant__ CUtensorMap tm) {
   using C = typename CT<T>::type;
   using PL = PlanD<N>;
   constexpr bool INV = PASS == SP_ZINV || PASS == SP_YINV;
-  using TL = StagedTile<T, N, W, INV>;
+  using TL = StagedTile<T, N, W, INV, KK>;
   using SPL = StagedPlan<PASS, MODE>;
-  constexpr int K = PL::K, M = PL::M, P = PL::P, R1 = PL::R1, R2 = PL::R2, TPL = PL::TPL, J1 = PL::J1;
+  constexpr int K = KK, M = KK + 1, P = 2 * KK + 1, R1 = PL::R1, R2 = PL::R2, TPL = PL::TPL, J1 = PL::J1;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   C* stg = reinterpret_cast<C*>(smraw + TL::STG_OFF);
@@ -246,14 +252,14 @@ k_strided_s(PassArgs a, const __grid_constant__ CUtensorMap tm) {
       static_for<0, R1>([&](auto nc) {
         constexpr int n1 = decltype(nc)::value;
         const int p = R2 * n1 + t + j * TPL;
-        if constexpr (INV && ZeroInputs<N>::zero(n1)) {
+        if constexpr (INV && ZeroInputs<N, KK>::zero(n1)) {
           in[j][n1] = zero;  // in the zero band for every column: not read
         } else if constexpr (INV) {
           int k;
-          if (!act || !k_of_pos<N>(p, k)) {
+          if (!act || !k_of_pos<N, KK>(p, k)) {
             in[j][n1] = zero;
           } else {
-            const C v = stg[(k + K) * W + w];
+            const C v = shift_in<SHIFT, KK>(stg[(k + K) * W + w], a.phase, k);
             if (kind == 0) {
               in[j][n1] = v;
             } else {
@@ -263,7 +269,9 @@ k_strided_s(PassArgs a, const __grid_constant__ CUtensorMap tm) {
               } else {
                 // second source of omega_x, read directly (y-inverse only)
                 const long long o = s2 * zs + ((long long)row * P + (k + K)) * M + ix;
-                in[j][n1] = PSC_OK_INDEX(o, (long long)Z_NSTREAM * zs, a.ctrl) ? csub(d, zb[o]) : zero;
+                in[j][n1] = PSC_OK_INDEX(o, (long long)Z_NSTREAM * zs, a.ctrl)
+                                ? csub(d, shift_in<SHIFT, KK>(zb[o], a.phase, k))
+                                : zero;
               }
             }
           }
@@ -275,7 +283,7 @@ k_strided_s(PassArgs a, const __grid_constant__ CUtensorMap tm) {
     if (leader && tr + 1 < SPL::NT) issue(tr + 1);
     if constexpr (PASS == SP_ZINV) {
       C* __restrict__ zo = static_cast<C*>(a.zb);
-      strided_fft_regs<T, N, W, +1, TL::TW_SMEM>(
+      strided_fft_regs<T, N, W, +1, TL::TW_SMEM, KK>(
           in,
           [&](int z, C v) {
             if (!act) return;
@@ -285,7 +293,7 @@ k_strided_s(PassArgs a, const __grid_constant__ CUtensorMap tm) {
           sm, tw, t, w);
     } else if constexpr (PASS == SP_YINV) {
       C* __restrict__ yo = static_cast<C*>(a.yb);
-      strided_fft_regs<T, N, W, +1, TL::TW_SMEM>(
+      strided_fft_regs<T, N, W, +1, TL::TW_SMEM, KK>(
           in,
           [&](int y, C v) {
             if (!act) return;
@@ -295,24 +303,24 @@ k_strided_s(PassArgs a, const __grid_constant__ CUtensorMap tm) {
           sm, tw, t, w);
     } else if constexpr (PASS == SP_YFWD) {
       C* __restrict__ yo = static_cast<C*>(a.yf);
-      strided_fft_regs<T, N, W, -1, TL::TW_SMEM>(
+      strided_fft_regs<T, N, W, -1, TL::TW_SMEM, KK>(
           in,
           [&](int k, C v) {
             int ky;
-            if (!act || !k_of_pos<N>(k, ky)) return;
+            if (!act || !k_of_pos<N, KK>(k, ky)) return;
             const long long idx = out * zs + ((long long)row * P + (ky + K)) * M + ix;
-            if (PSC_OK_INDEX(idx, 4 * zs, a.ctrl)) yo[idx] = v;
+            if (PSC_OK_INDEX(idx, 4 * zs, a.ctrl)) yo[idx] = shift_out<SHIFT, KK>(v, a.phase, ky);
           },
           sm, tw, t, w);
     } else {
       C* __restrict__ ro = static_cast<C*>(a.rb);
-      strided_fft_regs<T, N, W, -1, TL::TW_SMEM>(
+      strided_fft_regs<T, N, W, -1, TL::TW_SMEM, KK>(
           in,
           [&](int k, C v) {
             int kz;
-            if (!act || !k_of_pos<N>(k, kz)) return;
+            if (!act || !k_of_pos<N, KK>(k, kz)) return;
             const long long idx = out * S + ((long long)(kz + K) * P + row) * M + ix;
-            if (PSC_OK_INDEX(idx, 4 * S, a.ctrl)) ro[idx] = v;
+            if (PSC_OK_INDEX(idx, 4 * S, a.ctrl)) ro[idx] = shift_out<SHIFT, KK>(v, a.phase, kz);
           },
           sm, tw, t, w);
     }

@@ -594,15 +594,13 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : PSC_X2_MINB) k_xpass
 // latency overlaps at least three transforms, and the transforms read their
 // inputs from shared memory.
 // ---------------------------------------------------------------------------
-template <typename T, int N> struct X2SCfg {
+template <typename T, int N, int KK = (N - 1) / 3> struct X2SCfg {
   using C = typename CT<T>::type;
   using XC = X2Cfg<T, N>;
 #ifndef PSC_X2S_ROWS
 #define PSC_X2S_ROWS 6
 #endif
-  static constexpr int ROWS = PSC_X2S_ROWS;
-  static constexpr int THREADS = XC::TH * ROWS;
-  static constexpr int M = XC::K + 1;
+  static constexpr int M = KK + 1;
   static constexpr int NA = 6, NB = 3;  // streams Y_UX..Y_DYUX, Y_PHI..Y_DZPHI
 #ifndef PSC_X2S_STAGE_B
 #define PSC_X2S_STAGE_B 1
@@ -612,6 +610,15 @@ template <typename T, int N> struct X2SCfg {
   static constexpr unsigned ROW_BYTES = (unsigned)(M * sizeof(C));
   static constexpr size_t STAGE_BYTES = (size_t)(NA + (STAGE_B ? NB : 0)) * ROW_BYTES;
   static constexpr size_t GROUP_BYTES = STAGE_BYTES + XC::LINE_BYTES;
+  // rows in flight: PSC_X2S_ROWS, fewer where longer rows (the phase-shift
+  // sphere's cube) would not fit shared memory
+  static constexpr int rows_fit() {
+    int r = PSC_X2S_ROWS;
+    while (r > 1 && GROUP_BYTES * r + XC::TW_BYTES + 2 * r * 8 > 227 * 1024) --r;
+    return r;
+  }
+  static constexpr int ROWS = rows_fit();
+  static constexpr int THREADS = XC::TH * ROWS;
   static constexpr size_t TW_OFF = GROUP_BYTES * ROWS;
   static constexpr size_t BAR_OFF = TW_OFF + XC::TW_BYTES;
   static constexpr size_t SMEM = BAR_OFF + 2 * ROWS * sizeof(unsigned long long);
@@ -620,11 +627,11 @@ template <typename T, int N> struct X2SCfg {
                 "staged streams are contiguous");
 };
 
-template <typename T, int N>
-__global__ void __launch_bounds__(X2SCfg<T, N>::THREADS, 1) k_xpass2s(PassArgs a) {
+template <typename T, int N, int KK = (N - 1) / 3, bool SHIFT = false>
+__global__ void __launch_bounds__(X2SCfg<T, N, KK>::THREADS, 1) k_xpass2s(PassArgs a) {
   using C = typename CT<T>::type;
   using XC = X2Cfg<T, N>;
-  using SC = X2SCfg<T, N>;
+  using SC = X2SCfg<T, N, KK>;
   static_assert(SC::OK, "staged x pass: rows must be 16-byte multiples and fit shared memory");
   constexpr int TH = XC::TH, G = XC::G, ROWS = SC::ROWS, M = SC::M;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -696,7 +703,7 @@ __global__ void __launch_bounds__(X2SCfg<T, N>::THREADS, 1) k_xpass2s(PassArgs a
       if (SC::STAGE_B || st < SC::NA) return stg[st * M + kx];
       return row[st * ys + kx];
     };
-    ok = x2_rhs_row<T, N>(
+    ok = x2_rhs_row<T, N, false, KK, SHIFT>(
         Y,
         [&] {
           if (next < nlines) {
@@ -721,7 +728,7 @@ __global__ void __launch_bounds__(X2SCfg<T, N>::THREADS, 1) k_xpass2s(PassArgs a
             }
           }
         },
-        xb, line, ys, ex, q, scale, a.want_umax != 0, um, a.ctrl);
+        xb, line, ys, ex, q, scale, a.want_umax != 0, um, a.ctrl, a.phase);
     if (!ok) break;
   }
   if (!ok) {

@@ -12,6 +12,7 @@ def sparse_modes(N, seed, K, sphere):
     with conjugate partners on kx = 0; amplitudes O(N^3)."""
     rng = np.random.default_rng(seed)
     if sphere:
+        K = O.sphere_halfwidth(N)  # the sphere's edge (the stored cube may be one plane wider)
         e = int(K / np.sqrt(2.0))  # |(e, e, 0)| stays inside the sphere
         ks = [(1, 0, 1), (0, 2, -1), (2, 1, 0), (1, -1, 2), (3, 2, -2), (K, 0, 1), (0, K - 1, 2),
               (e, -e, 0), (e - 3, 2, e), (0, 1, 1), (K // 3, K // 2, -K // 2), (2, 0, 0)]

@@ -117,4 +117,8 @@ def test_dealiasing_and_form_validation(lib):
     # compact shapes follow the retained half-width
     assert B.compact_shape(520) == (4, 347, 347, 174)
     assert B.compact_shape(520, PS) == (4, 491, 491, 246)
-    assert B.compact_shape(1024, PS) == (4, 965, 965, 483)
+    # the sphere's cube at 1024^3: half-width 482 (9 k^2 < 2 N^2) widened to 483
+    # so that a kx row holds an even number of values (TMA-staged passes)
+    assert B.compact_shape(1024, PS) == (4, 967, 967, 484)
+    assert B.compact_shape(256, PS) == (4, 243, 243, 122)
+    assert B.compact_shape(512, PS) == (4, 483, 483, 242)

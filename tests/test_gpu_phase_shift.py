@@ -78,9 +78,12 @@ def gpu_rhs(dev, p, x):
 
 def test_layout_is_the_spheres_cube(dev):
     for N in (8, 16, 32, 64, 256):
-        K = Ks(N)
-        assert K == O.sphere_halfwidth(N)
-        assert 9 * K * K < 2 * N * N <= 9 * (K + 1) * (K + 1)
+        K, ks = Ks(N), O.sphere_halfwidth(N)
+        assert 9 * ks * ks < 2 * N * N <= 9 * (ks + 1) * (ks + 1)
+        # the sphere's own half-width, or one more so that a kx row holds an
+        # even number of values (the planes added lie outside the sphere)
+        assert K == ks or (K == ks + 1 and ks % 2 == 0 and 2 * K + 1 <= N)
+        assert (K + 1) % 2 == 0 or 2 * K + 3 > N
         p = B.Params(N=N, precision=B.FP32_MIXED, dealias=PS)
         sim = B.Simulation(p, device=dev)
         assert sim.get_state().shape == (4, 2 * K + 1, 2 * K + 1, K + 1)
@@ -198,7 +201,7 @@ def test_phase_shift_records_match_oracle(dev, prec):
     sim.close()
     uh, _, recs, _, _ = O.run(oparams(p), 15, with_records=True)
     assert len(recs) == len(got) == 4
-    assert len(got[0][1]) == O.num_shells(N, O.DEALIAS_PHASE_SHIFT) == Ks(N) + 2
+    assert len(got[0][1]) == O.num_shells(N, O.DEALIAS_PHASE_SHIFT) == O.sphere_halfwidth(N) + 2
     tol = 1e-10 if prec == B.FP64 else 2e-4
     keys = ("K", "K_phys", "eps", "eps_phys", "chi", "chi_phys", "phi_var", "umax", "dt", "A", "E_forced")
     scale = {k: max(abs(r[k]) for r in recs) for k in keys}
