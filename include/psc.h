@@ -234,8 +234,10 @@ psc_status psc_batch_destroy(psc_batch* b);
  * by rewriting the table on `stream`, ordered after the steps already
  * enqueued; the captured graph stays valid, so boxes join and leave between
  * steps without a new capture.  Members must not be used on their own while a
- * batch step may be running (synchronise `stream` first).  psc_batch_step()
- * and psc_batch_destroy() serve both kinds of batch. */
+ * batch step may be running (synchronise `stream` first), and a member must be
+ * taken out of the table (psc_batch_set_members without it) before it is
+ * destroyed: the table holds its device addresses.  psc_batch_step() and
+ * psc_batch_destroy() serve both kinds of batch. */
 #define PSC_BATCH_MAX_BOXES 4096
 typedef enum { PSC_BATCH_GRAPH = 0, PSC_BATCH_PERSISTENT = 1 } psc_batch_mode;
 psc_status psc_batch_table_bytes(int32_t max_boxes, size_t* bytes);
