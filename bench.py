@@ -65,6 +65,8 @@ def parse():
                     help="only time the right-hand-side X pass of the --N grid (FP32-mixed) on ROWS rows of "
                          "synthetic input (psc_xpass_probe; a small footprint for counter captures): "
                          "--warmup launches, then --steps timed launches")
+    ap.add_argument("--paper-example-out", default="",
+                    help="with --paper-example-steps: append each record to this file as it is taken (JSON lines)")
     ap.add_argument("--paper-example-steps", type=int, default=0,
                     help="with --paper-example: also run the FP32-mixed phase-shift case this many steps "
                          "from its IC, a record every 100 steps (time series of Table 1 and Eqs. 11-12)")
@@ -562,7 +564,7 @@ def run_dealias(every=10):
     return out
 
 
-def run_paper_example(steps=20, run_steps=0):
+def run_paper_example(steps=20, run_steps=0, out_path=""):
     """The example of the paper's section 3 at N = 520: nu = 8e-4, kF = 2, the
     deterministic forcing that holds the band energy, dt = 5e-4 held fixed,
     records every 100 steps, IC with the Eq. 9 spectrum at 6 times the energy
@@ -614,22 +616,53 @@ def run_paper_example(steps=20, run_steps=0):
         sim = psc.Simulation(p, device="cuda:0")
         sim.init_field()
         series = []
+        sink = open(out_path, "a") if out_path else None
         t0 = time.perf_counter()
+        te_t = 0.0  # elapsed time in large-eddy turnover times, T_e taken record by record
         for n in range(0, run_steps + 1, 100):
             if n:
                 sim.step(100)
             r, _, _ = sim.stats()
-            series.append({"step": r["step"], "t": round(r["t"], 4), "t_over_Te": round(r["t"] / r["Te"], 3),
-                           "K": round(r["K"], 5), "eps": round(r["eps"], 5), "Re_lambda": round(r["Re_lambda"], 2),
-                           "kmax_eta_sqrt2": round(r["kmax_eta_sqrt2"], 4), "cfl": round(r["cfl"], 4),
-                           "skew": [round(v, 4) for v in r["skew"]], "flat": [round(v, 4) for v in r["flat"]],
+            if series:
+                te_t += (r["t"] - series[-1]["t"]) / (0.5 * (r["Te"] + series[-1]["Te"]))
+            series.append({"step": r["step"], "t": round(r["t"], 4), "Te": round(r["Te"], 5),
+                           "t_over_Te": round(te_t, 3), "K": round(r["K"], 5), "eps": round(r["eps"], 5),
+                           "Re_lambda": round(r["Re_lambda"], 2), "kmax_eta_sqrt2": round(r["kmax_eta_sqrt2"], 4),
+                           "cfl": round(r["cfl"], 4), "skew": [round(v, 4) for v in r["skew"]],
+                           "flat": [round(v, 4) for v in r["flat"]],
                            "skew_phi": [round(v, 4) for v in r["skew_phi"]],
-                           "flat_phi": [round(v, 4) for v in r["flat_phi"]]})
+                           "flat_phi": [round(v, 4) for v in r["flat_phi"]],
+                           "prod_over_chi": round(r["phi_prod"] / r["chi"], 4) if r["chi"] > 0 else None})
+            if sink:
+                sink.write(json.dumps(series[-1]) + "\n")
+                sink.flush()
+        if sink:
+            sink.close()
         out["run_fp32_mixed_phase_shift"] = {"steps": run_steps, "wall_s": time.perf_counter() - t0,
-                                             "records": series}
+                                             "stationary": stationary_means(series), "records": series}
         sim.close()
         torch.cuda.empty_cache()
     return out
+
+
+def stationary_means(series, frac=0.4):
+    """Means of the paper's stationary-state quantities (section 3) over the
+    records of the last `frac` of the run, counted in large-eddy turnover
+    times: Re_lambda, the velocity-gradient skewness and flatness (averaged
+    over the three diagonal components), the skewness and flatness of the
+    scalar gradient along the mean gradient, and production over dissipation
+    of the scalar variance."""
+    if len(series) < 2:
+        return None
+    t_end = series[-1]["t_over_Te"]
+    win = [r for r in series if r["t_over_Te"] >= (1.0 - frac) * t_end]
+    mean = lambda f: sum(f(r) for r in win) / len(win)
+    return {"window_t_over_Te": [win[0]["t_over_Te"], t_end], "records": len(win),
+            "Re_lambda": mean(lambda r: r["Re_lambda"]),
+            "skew_du": mean(lambda r: sum(r["skew"]) / 3.0), "flat_du": mean(lambda r: sum(r["flat"]) / 3.0),
+            "skew_dphi_2": mean(lambda r: r["skew_phi"][1]), "flat_dphi_2": mean(lambda r: r["flat_phi"][1]),
+            "prod_over_chi": mean(lambda r: r["prod_over_chi"] or 0.0),
+            "kmax_eta_sqrt2": mean(lambda r: r["kmax_eta_sqrt2"])}
 
 
 def run_companion(N=512, steps=200, every=10):
@@ -719,7 +752,8 @@ def main():
         print(json.dumps({"dealias": run_dealias()}), flush=True)
         return 0
     if a.paper_example:
-        print(json.dumps({"paper_example_520": run_paper_example(run_steps=a.paper_example_steps)}), flush=True)
+        print(json.dumps({"paper_example_520": run_paper_example(run_steps=a.paper_example_steps,
+                                                                         out_path=a.paper_example_out)}), flush=True)
         return 0
 
     import torch

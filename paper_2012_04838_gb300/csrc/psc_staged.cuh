@@ -117,6 +117,8 @@ __device__ __forceinline__ void strided_fft_regs(typename CT<T>::type (&in)[Plan
 // times the source minus stream s2 (omega_x = d_y u_z - d_z u_y).
 // MODE: z-inverse 0 (7 streams) or 1 (8, for the statistics and the convective
 // form); y-inverse YMODE_RHS (9), YMODE_STATS (11) or YMODE_CONVECTIVE (12).
+// Transforms of one source run one after another: the second reads the tile
+// still staged instead of copying it again (reuses()).
 template <int PASS, int MODE> struct StagedPlan {
   static constexpr int NT = PASS == SP_ZINV   ? (MODE ? 8 : 7)
                             : PASS == SP_YINV ? (MODE == YMODE_CONVECTIVE ? 12 : MODE == YMODE_STATS ? 11 : 9)
@@ -124,30 +126,41 @@ template <int PASS, int MODE> struct StagedPlan {
   __device__ __forceinline__ static void get(int tr, int& src, int& kind, int& s2, int& out) {
     s2 = 0;
     if constexpr (PASS == SP_ZINV) {
-      switch (tr) {
+      // u_x, d_z u_x, u_y, d_z u_y, u_z, [d_z u_z], phi, d_z phi
+      int t = tr;
+      if (MODE) {
+        if (t == 5) { src = 2; kind = 1; out = Z_DZUZ; return; }
+        if (t > 5) --t;
+      }
+      switch (t) {
         case 0: src = 0; kind = 0; out = Z_UX; break;
-        case 1: src = 1; kind = 0; out = Z_UY; break;
-        case 2: src = 2; kind = 0; out = Z_UZ; break;
+        case 1: src = 0; kind = 1; out = Z_DZUX; break;
+        case 2: src = 1; kind = 0; out = Z_UY; break;
         case 3: src = 1; kind = 1; out = Z_DZUY; break;
-        case 4: src = 0; kind = 1; out = Z_DZUX; break;
+        case 4: src = 2; kind = 0; out = Z_UZ; break;
         case 5: src = 3; kind = 0; out = Z_PHI; break;
-        case 6: src = 3; kind = 1; out = Z_DZPHI; break;
-        default: src = 2; kind = 1; out = Z_DZUZ; break;
+        default: src = 3; kind = 1; out = Z_DZPHI; break;
       }
     } else if constexpr (PASS == SP_YINV) {
-      switch (tr) {
+      // u_x, d_y u_x, u_y, [d_y u_y], u_z, omega_x, d_z u_x, phi, d_y phi,
+      // d_z phi, [d_z u_z, [d_z u_y]]
+      int t = tr;
+      if (MODE != YMODE_RHS) {
+        if (t == 3) { src = Z_UY; kind = 1; out = Y_DYUY; return; }
+        if (t > 3) --t;
+      }
+      switch (t) {
         case 0: src = Z_UX; kind = 0; out = Y_UX; break;
-        case 1: src = Z_UY; kind = 0; out = Y_UY; break;
-        case 2: src = Z_UZ; kind = 0; out = Y_UZ; break;
-        case 3:  // omega_x = d_y u_z - d_z u_y (convective form: d_y u_z alone)
+        case 1: src = Z_UX; kind = 1; out = Y_DYUX; break;
+        case 2: src = Z_UY; kind = 0; out = Y_UY; break;
+        case 3: src = Z_UZ; kind = 0; out = Y_UZ; break;
+        case 4:  // omega_x = d_y u_z - d_z u_y (convective form: d_y u_z alone)
           src = Z_UZ; kind = MODE == YMODE_CONVECTIVE ? 1 : 2; s2 = Z_DZUY; out = Y_WX; break;
-        case 4: src = Z_DZUX; kind = 0; out = Y_DZUX; break;
-        case 5: src = Z_UX; kind = 1; out = Y_DYUX; break;
+        case 5: src = Z_DZUX; kind = 0; out = Y_DZUX; break;
         case 6: src = Z_PHI; kind = 0; out = Y_PHI; break;
         case 7: src = Z_PHI; kind = 1; out = Y_DYPHI; break;
         case 8: src = Z_DZPHI; kind = 0; out = Y_DZPHI; break;
-        case 9: src = Z_UY; kind = 1; out = Y_DYUY; break;
-        case 10: src = Z_DZUZ; kind = 0; out = Y_DZUZ; break;
+        case 9: src = Z_DZUZ; kind = 0; out = Y_DZUZ; break;
         default: src = Z_DZUY; kind = 0; out = Y_DZUY; break;
       }
     } else {
@@ -155,6 +168,14 @@ template <int PASS, int MODE> struct StagedPlan {
       kind = 0;
       out = tr;
     }
+  }
+  // transform tr reads the same tile as transform tr - 1
+  __device__ __forceinline__ static bool reuses(int tr) {
+    if (tr == 0) return false;
+    int s0, s1, k, x, o;
+    get(tr - 1, s0, k, x, o);
+    get(tr, s1, k, x, o);
+    return s0 == s1;
   }
 };
 
@@ -232,20 +253,21 @@ k_strided_s(PassArgs a, const __grid_constant__ CUtensorMap tm) {
   for (int tr = 0; tr < SPL::NT; ++tr) {
     int src, kind, s2, out;
     SPL::get(tr, src, kind, s2, out);
-    // one thread polls the barrier while the others wait at the CTA barrier
-    // (which also orders the last transform's exchange reads before this
-    // one's writes); the barrier makes the tile visible to every thread
-    const bool landed = mbar_wait(bar, parity, &a.ctrl->err);
-    if (!__syncthreads_and(landed)) {
-      // the tile did not arrive in time: report, give it a bounded time to
-      // land in this CTA's shared memory, and stop
-      if (leader) {
-        atomicOr(&a.ctrl->err, 4);
-        mbar_wait(bar, parity);
+    if (!SPL::reuses(tr)) {
+      // every thread polls the barrier, and the CTA barrier shares the
+      // outcome (a transform that reuses the staged tile has nothing to wait for)
+      const bool landed = mbar_wait(bar, parity, &a.ctrl->err);
+      if (!__syncthreads_and(landed)) {
+        // the tile did not arrive in time: report, give it a bounded time to
+        // land in this CTA's shared memory, and stop
+        if (leader) {
+          atomicOr(&a.ctrl->err, 4);
+          mbar_wait(bar, parity);
+        }
+        return;
       }
-      return;
+      parity ^= 1u;
     }
-    parity ^= 1u;
     C in[J1][R1];
 #pragma unroll
     for (int j = 0; j < J1; ++j)
@@ -279,8 +301,10 @@ k_strided_s(PassArgs a, const __grid_constant__ CUtensorMap tm) {
           in[j][n1] = stg[p * W + w];
         }
       });
-    __syncthreads();  // the staging tile is free
-    if (leader && tr + 1 < SPL::NT) issue(tr + 1);
+    // the staging tile is free (unless the next transform reads it again), and
+    // the last transform's exchange reads come before this one's writes
+    __syncthreads();
+    if (leader && tr + 1 < SPL::NT && !SPL::reuses(tr + 1)) issue(tr + 1);
     if constexpr (PASS == SP_ZINV) {
       C* __restrict__ zo = static_cast<C*>(a.zb);
       strided_fft_regs<T, N, W, +1, TL::TW_SMEM, KK>(
