@@ -34,7 +34,8 @@ template <typename T, int N> struct X2Cfg {
   //   T1[a][tid]  = wN^(a tid)             (inverse step after the first DFT-16)
   //   T3[k1][tid] = wN^(ra (rk0 + G k1))   (forward step before the exchange)
   //   T2[b][k0]   = wN^(16 b k0)           (between the lane DFT and the DFT-16 over b)
-  // laid out so the 32 lanes of a warp read consecutive entries
+  // laid out so the 32 lanes of a warp read consecutive entries (FP32: pairs
+  // of consecutive a, k1 or b side by side, see tw_index)
   static constexpr size_t TW_BYTES = (size_t)(2 * 16 * TH + 16 * G) * sizeof(C);
   static constexpr size_t SMEM = LINE_BYTES * ROWS + ACC_BYTES + TW_BYTES;
   static constexpr int K = (N - 1) / 3;
@@ -133,6 +134,27 @@ template <typename C> struct X2Roles {
   const C* t3;
 };
 
+// Twiddle tables hold entries (e, j) (e < 16: a, b or k1; j: the thread's
+// column) in pairs of consecutive e for FP32, so one 128-bit shared load
+// brings the twiddles of e and e + 1; FP64 entries are 16 bytes already.
+template <typename T, int J> __device__ __forceinline__ int tw_index(int e, int j) {
+  if constexpr (sizeof(T) == 4) return (((e >> 1) * J + j) << 1) | (e & 1);
+  else return e * J + j;
+}
+// the twiddles of e and e + 1 (e even) for column j
+template <typename T, int J>
+__device__ __forceinline__ void tw_pair(const typename CT<T>::type* t, int e, int j, typename CT<T>::type& w0,
+                                        typename CT<T>::type& w1) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 p = *reinterpret_cast<const float4*>(t + tw_index<T, J>(e, j));
+    w0 = make_float2(p.x, p.y);
+    w1 = make_float2(p.z, p.w);
+  } else {
+    w0 = t[tw_index<T, J>(e, j)];
+    w1 = t[tw_index<T, J>(e + 1, j)];
+  }
+}
+
 // Inverse transform of a Hermitian-packed half spectrum (two real fields):
 // Z[p] = X1[p] + i X2[p] (p <= K, imaginary parts dropped at p = 0),
 // conj(X1[N-p]) + i conj(X2[N-p]) (p >= N-K), 0 elsewhere.  On return
@@ -184,10 +206,12 @@ __device__ __forceinline__ void x2inv(const SPEC& spec, typename CT<T>::type (&z
   });
   x2_first_inverse<N, KK>::template run<T, C>(v);  // over k2 -> a
 #pragma unroll
-  for (int a = 0; a < 16; ++a) {
-    C w = v[a];
-    if (a > 0) w = cmulc(w, q.t1[a * TH + q.tid]);  // wN^(-a j)
-    ex[a * ROW + q.tid] = w;
+  for (int a = 0; a < 16; a += 2) {
+    C w0, w1;
+    tw_pair<T, TH>(q.t1, a, q.tid, w0, w1);
+    const C u0 = a > 0 ? cmulc(v[a], w0) : v[a];  // wN^(-a j)
+    ex[a * ROW + q.tid] = u0;
+    ex[(a + 1) * ROW + q.tid] = cmulc(v[a + 1], w1);
   }
   row_sync<TH>(q.bar);
 #pragma unroll
@@ -196,7 +220,12 @@ __device__ __forceinline__ void x2inv(const SPEC& spec, typename CT<T>::type (&z
   Dft<16, +1>::template run<T, C>(z);  // over k1 -> b
   if (q.rk0 > 0) {
 #pragma unroll
-    for (int b = 1; b < 16; ++b) z[b] = cmulc(z[b], q.t2[b * G + q.rk0]);  // wN^(-16 b k0)
+    for (int b = 0; b < 16; b += 2) {  // wN^(-16 b k0)
+      C w0, w1;
+      tw_pair<T, G>(q.t2, b, q.rk0, w0, w1);
+      if (b > 0) z[b] = cmulc(z[b], w0);
+      z[b + 1] = cmulc(z[b + 1], w1);
+    }
   }
   lane_dft<T, G, +1>(z, q.rr);  // over k0 -> c
   if constexpr (SCALE) {
@@ -217,15 +246,25 @@ __device__ __forceinline__ void x2fwd(typename CT<T>::type (&z)[16], const OUT& 
   lane_dft<T, G, -1>(z, q.rr);  // over c -> k0
   if (q.rk0 > 0) {
 #pragma unroll
-    for (int b = 1; b < 16; ++b) z[b] = cmul(z[b], q.t2[b * G + q.rk0]);  // wN^(16 b k0)
+    for (int b = 0; b < 16; b += 2) {  // wN^(16 b k0)
+      C w0, w1;
+      tw_pair<T, G>(q.t2, b, q.rk0, w0, w1);
+      if (b > 0) z[b] = cmul(z[b], w0);
+      z[b + 1] = cmul(z[b + 1], w1);
+    }
   }
   Dft<16, -1>::template run<T, C>(z);  // over b -> k1
 #pragma unroll
-  for (int k1 = 0; k1 < 16; ++k1) {
+  for (int k1 = 0; k1 < 16; k1 += 2) {
+    C w0, w1;
+    tw_pair<T, TH>(q.t3, k1, q.tid, w0, w1);  // wN^(a (k0 + G k1))
     const int j = q.rk0 + G * k1;
-    C w = z[k1];
-    if (q.ra > 0 && j > 0) w = cmul(w, q.t3[k1 * TH + q.tid]);  // wN^(a (k0 + G k1))
-    ex[q.ra * ROW + j] = w;
+    C u0 = z[k1];
+    if (q.ra > 0 && j > 0) u0 = cmul(u0, w0);
+    ex[q.ra * ROW + j] = u0;
+    C u1 = z[k1 + 1];
+    if (q.ra > 0) u1 = cmul(u1, w1);
+    ex[q.ra * ROW + j + G] = u1;
   }
   row_sync<TH>(q.bar);
   C v[16];
@@ -261,10 +300,10 @@ __device__ __forceinline__ void x2_twiddles(typename CT<T>::type* t1, const type
   for (int i = threadIdx.x; i < 16 * TH; i += blockDim.x) {
     const int e = i / TH, tid = i % TH;  // e = a for T1, k1 for T3
     const int ra = tid / G, rk0 = bitrev_lane<G>(tid % G);
-    t1[i] = tw[e * tid];
-    t3[i] = tw[ra * (rk0 + G * e)];
+    t1[tw_index<T, TH>(e, tid)] = tw[e * tid];
+    t3[tw_index<T, TH>(e, tid)] = tw[ra * (rk0 + G * e)];
   }
-  for (int i = threadIdx.x; i < 16 * G; i += blockDim.x) t2[i] = tw[16 * (i / G) * (i % G)];
+  for (int i = threadIdx.x; i < 16 * G; i += blockDim.x) t2[tw_index<T, G>(i / G, i % G)] = tw[16 * (i / G) * (i % G)];
   q.t1 = t1;
   q.t2 = t2;
   q.t3 = t3;
