@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "psc.h"
 #include "psc_kernels.cuh"
 
@@ -188,8 +190,23 @@ cudaEvent_t take_event(psc_sim* s) {
   return e;
 }
 
-// Run `launch` (which enqueues kernels on s->st) as `n` launches of `kind`.
+// NVTX range names of the kernel kinds (psc_kernel_kind)
+const char* const kKindName[PSC_K_NKIND] = {"psc forcing", "psc z-inverse", "psc y-inverse", "psc x pass",
+                                            "psc y-forward", "psc z-forward", "psc combine", "psc other"};
+
+// An NVTX range on the calling thread for the life of the object (nothing
+// happens unless an NVTX tool is attached to the process)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Run `launch` (which enqueues kernels on s->st) as `n` launches of `kind`,
+// inside an NVTX range named for the kind.
 template <class F> void launch(psc_sim* s, int kind, int n, F&& f) {
+  NvtxRange r(kKindName[kind]);
   s->launches += n;
   if (!s->profiling) {
     f();
@@ -832,6 +849,7 @@ psc_status psc_init_field(psc_sim* s) {
 psc_status psc_step(psc_sim* s, int32_t nsteps) {
   if (!s) return fail(PSC_EINVAL, "null sim");
   if (nsteps < 0) return fail(PSC_EINVAL, "nsteps must be >= 0");
+  NvtxRange r("psc_step");
   return s->fp64 ? do_step<double>(s, nsteps) : do_step<float>(s, nsteps);
 }
 
@@ -851,6 +869,7 @@ psc_status psc_spectra_and_stats(psc_sim* s, double* Ek, double* Ephi, int32_t c
                                  psc_stats* out) {
   if (!s) return fail(PSC_EINVAL, "null sim");
   if (cap < 0) return fail(PSC_EINVAL, "negative capacity");
+  NvtxRange r("psc_spectra_and_stats");
   return s->fp64 ? do_stats<double>(s, Ek, Ephi, cap, nshell, out)
                  : do_stats<float>(s, Ek, Ephi, cap, nshell, out);
 }
@@ -1109,6 +1128,7 @@ psc_status psc_batch_create(psc_sim* const* sims, int32_t n, void* stream, psc_b
 psc_status psc_batch_step(psc_batch* b, int32_t nsteps) {
   if (!b) return fail(PSC_EINVAL, "null batch");
   if (nsteps < 0) return fail(PSC_EINVAL, "nsteps must be >= 0");
+  NvtxRange r(b->mode == PSC_BATCH_PERSISTENT ? "psc_batch_step persistent" : "psc_batch_step graph");
   for (int k = 0; k < nsteps; ++k) PSC_CUDA(cudaGraphLaunch(b->exec, b->st));
   for (size_t i = 0; i < b->sims.size(); ++i) {
     b->sims[i]->step += nsteps;
