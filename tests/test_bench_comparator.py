@@ -28,3 +28,23 @@ def test_plain_comparator_equals_the_oracle_rhs(N):
     idx = np.arange(-K, K + 1) % N
     full[:, idx[:, None], idx[None, :], :K + 1] = 0
     assert np.abs(full).max() < 1e-12 * np.abs(want).max()
+
+
+def test_stationary_window_means_of_the_paper_example():
+    """bench.stationary_means averages the last 40% of a run, counted in
+    large-eddy turnover times, and takes the scalar-gradient moments along
+    the mean gradient (component 2)."""
+    import bench
+    series = []
+    for i in range(11):  # t/T_e = 0, 1, ..., 10
+        series.append({"t_over_Te": float(i), "Re_lambda": 100.0 + 10 * i,
+                       "skew": [-0.5, -0.6, -0.7], "flat": [6.0, 7.0, 8.0],
+                       "skew_phi": [0.0, 1.0 + 0.1 * i, 0.0], "flat_phi": [9.0, 20.0, 9.0],
+                       "prod_over_chi": None if i == 0 else 1.0, "kmax_eta_sqrt2": 1.5})
+    m = bench.stationary_means(series)
+    assert m["window_t_over_Te"] == [6.0, 10.0] and m["records"] == 5
+    assert abs(m["Re_lambda"] - 180.0) < 1e-12          # mean of 160 ... 200
+    assert abs(m["skew_du"] + 0.6) < 1e-12 and abs(m["flat_du"] - 7.0) < 1e-12
+    assert abs(m["skew_dphi_2"] - 1.8) < 1e-12 and m["flat_dphi_2"] == 20.0
+    assert m["prod_over_chi"] == 1.0
+    assert bench.stationary_means(series[:1]) is None
