@@ -1131,19 +1131,22 @@ template <typename T, int N> struct Passes {
       k_xpass<T, N, MODE><<<xgrid(), dim3(32 * XCfg<T, N>::WARPS), sm, a.st>>>(a);
     }
   }
+  // the staged x pass of the right-hand side (rotational or convective form)
+  template <int MODE> static void xpass_staged(const PassArgs& a) {
+    constexpr int KD = (N - 1) / 3;
+    using SC = X2SCfg<T, N, KD, MODE>;
+    const long long rows = (long long)N * N / SC::ROWS;
+    const int grid = (int)(rows < sm_count() ? rows : sm_count());
+    prep(k_xpass2s<T, N, KD, false, MODE>, SC::SMEM);
+    k_xpass2s<T, N, KD, false, MODE><<<grid, SC::THREADS, SC::SMEM, a.st>>>(a);
+  }
   static void xpass_reg(const PassArgs& a, int mode) {
     if (mode == XMODE_PRESSURE) return xpass_plain<XMODE_PRESSURE>(a);
-    if (mode == XMODE_CONVECTIVE) return xpass_plain<XMODE_CONVECTIVE>(a);
     if constexpr (X2S) {
-      if (mode == XMODE_RHS) {
-        using SC = X2SCfg<T, N>;
-        const long long rows = (long long)N * N / SC::ROWS;
-        const int grid = (int)(rows < sm_count() ? rows : sm_count());
-        prep(k_xpass2s<T, N>, SC::SMEM);
-        k_xpass2s<T, N><<<grid, SC::THREADS, SC::SMEM, a.st>>>(a);
-        return;
-      }
+      if (mode == XMODE_RHS) return xpass_staged<XMODE_RHS>(a);
+      if (mode == XMODE_CONVECTIVE) return xpass_staged<XMODE_CONVECTIVE>(a);
     }
+    if (mode == XMODE_CONVECTIVE) return xpass_plain<XMODE_CONVECTIVE>(a);
     if constexpr (XROW) {
       (void)a;
       (void)mode;

@@ -399,9 +399,14 @@ __device__ __forceinline__ bool x2_rhs_row(const YF& Y, const HA& after_a, const
 
 // The convective form of one row: -(u.grad)u and u.grad phi from u, its nine
 // gradients and grad phi (8 inverse transforms of packed pairs, 2 forward).
-// With this stream set Y_WX holds d_y u_z and Y_DZUY holds d_z u_y.
-template <typename T, int N, int KK = (N - 1) / 3, bool SHIFT = false, class YF>
-__device__ __forceinline__ void x2_conv_row(const YF& Y, typename CT<T>::type* __restrict__ xb, long long line,
+// With this stream set Y_WX holds d_y u_z and Y_DZUY holds d_z u_y.  The
+// hooks as in x2_rhs_row: after_a() once UX, UY, UZ, DZUX, DYUX, DYUY and DZUY
+// are no longer read, wait_b() before WX, PHI, DYPHI, DZPHI and DZUZ are first
+// read (false aborts the row), after_b() once those are no longer read.
+// Returns false if aborted.
+template <typename T, int N, int KK = (N - 1) / 3, bool SHIFT = false, class YF, class HA, class WB, class HB>
+__device__ __forceinline__ bool x2_conv_row(const YF& Y, const HA& after_a, const WB& wait_b, const HB& after_b,
+                                            typename CT<T>::type* __restrict__ xb, long long line,
                                             long long ys, typename CT<T>::type* ex,
                                             const X2Roles<typename CT<T>::type>& q, T scale, bool want_umax, T& um,
                                             Ctrl* ctrl, const void* phase = nullptr) {
@@ -443,6 +448,7 @@ __device__ __forceinline__ void x2_conv_row(const YF& Y, typename CT<T>::type* _
   // (d3 u2, d1 u3): B = (u.grad) u2; A starts (u.grad) u3
   x2inv<T, N, false, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZUY, kx); x2 = mul_ik(Y(Y_UZ, kx), T(kx)); }, z, ex, q,
                      scale, phase);
+  after_a();
 #pragma unroll
   for (int b = 0; b < 16; ++b) {
     const T b2 = B[b] + u3[b] * z[b].x, c3 = u1[b] * z[b].y;
@@ -450,6 +456,7 @@ __device__ __forceinline__ void x2_conv_row(const YF& Y, typename CT<T>::type* _
     A[b] = c3;
   }
   x2fwd<T, N, KK, SHIFT>(z, out(0), ex, q, phase);
+  if (!wait_b()) return false;
   // (d2 u3, d3 u3): A = (u.grad) u3
   x2inv<T, N, false, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_WX, kx); x2 = Y(Y_DZUZ, kx); }, z, ex, q, scale, phase);
 #pragma unroll
@@ -461,9 +468,11 @@ __device__ __forceinline__ void x2_conv_row(const YF& Y, typename CT<T>::type* _
   for (int b = 0; b < 16; ++b) B[b] = u1[b] * z[b].x + u2[b] * z[b].y;
   // (dphi/dx3, 0)
   x2inv<T, N, false, KK, SHIFT>([&](int kx, C& x1, C& x2) { x1 = Y(Y_DZPHI, kx); x2 = zero; }, z, ex, q, scale, phase);
+  after_b();
 #pragma unroll
   for (int b = 0; b < 16; ++b) z[b] = mk(-A[b] * s2, (B[b] + u3[b] * z[b].x) * s2);  // (NL3, u.grad phi)
   x2fwd<T, N, KK, SHIFT>(z, out(2), ex, q, phase);
+  return true;
 }
 
 template <typename T>
@@ -519,7 +528,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : PSC_X2_MINB) k_xpass
       x2_rhs_row<T, N, MODE == XMODE_PRESSURE, KK, SHIFT>(Y, [] {}, [] { return true; }, [] {}, xb, line, ys, ex, q,
                                                           scale, a.want_umax != 0, um, a.ctrl, a.phase);
     } else if constexpr (MODE == XMODE_CONVECTIVE) {
-      x2_conv_row<T, N, KK, SHIFT>(Y, xb, line, ys, ex, q, scale, a.want_umax != 0, um, a.ctrl, a.phase);
+      x2_conv_row<T, N, KK, SHIFT>(Y, [] {}, [] { return true; }, [] {}, xb, line, ys, ex, q, scale,
+                                   a.want_umax != 0, um, a.ctrl, a.phase);
     } else {
       // statistics (Eqs. 11-13): per pair, partial sums of the thread's 16
       // points, added in FP64 to the thread's accumulators (reduced over the
@@ -624,33 +634,47 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : PSC_X2_MINB) k_xpass
 }
 
 // ---------------------------------------------------------------------------
-// Staged x pass (right-hand side, FP32, N = 1024).  One CTA per SM holds
-// X2SCfg::ROWS rows in flight; the nine input streams of each row are copied
-// into shared memory by bulk asynchronous copies (TMA engine) one row ahead,
-// in two groups completed on two mbarriers: UX..DYUX (read by the first three
-// inverse transforms) and PHI..DZPHI (read by the last two).  Each group of the
-// next row is issued as soon as the current row stops reading it, so global
-// latency overlaps at least three transforms, and the transforms read their
-// inputs from shared memory.
+// Staged x pass (right-hand side, rotational or convective form; FP32,
+// N = 1024).  One CTA per SM holds X2SCfg::ROWS rows in flight; the input
+// streams of each row are copied into shared memory by bulk asynchronous
+// copies (TMA engine) one row ahead, in two groups completed on two mbarriers:
+// group A, the streams of the first inverse transforms, and group B, those of
+// the last ones (X2SGroups).  Each group of the next row is issued as soon as
+// the current row stops reading it, so global latency overlaps several
+// transforms, and the transforms read their inputs from shared memory.
 // ---------------------------------------------------------------------------
-template <typename T, int N, int KK = (N - 1) / 3> struct X2SCfg {
+// Streams a staged row reads, as bit masks over the y-stage streams (a
+// stream's shared-memory slot is its index)
+template <int MODE> struct X2SGroups;
+template <> struct X2SGroups<XMODE_RHS> {
+  // UX..DYUX (the first three inverse transforms), PHI..DZPHI (the last two)
+  static constexpr unsigned A = (1u << Y_UX) | (1u << Y_UY) | (1u << Y_UZ) | (1u << Y_WX) | (1u << Y_DZUX) |
+                                (1u << Y_DYUX);
+  static constexpr unsigned B = (1u << Y_PHI) | (1u << Y_DYPHI) | (1u << Y_DZPHI);
+  static constexpr int SLOTS = Y_DZPHI + 1;
+};
+template <> struct X2SGroups<XMODE_CONVECTIVE> {
+  // u and the gradients of u1 and u2 (the first five inverse transforms); the
+  // gradient of u3 but d_x u3, and phi with its gradient (the last three)
+  static constexpr unsigned A = (1u << Y_UX) | (1u << Y_UY) | (1u << Y_UZ) | (1u << Y_DZUX) | (1u << Y_DYUX) |
+                                (1u << Y_DYUY) | (1u << Y_DZUY);
+  static constexpr unsigned B = (1u << Y_WX) | (1u << Y_PHI) | (1u << Y_DYPHI) | (1u << Y_DZPHI) | (1u << Y_DZUZ);
+  static constexpr int SLOTS = Y_DZUY + 1;
+};
+
+template <typename T, int N, int KK = (N - 1) / 3, int MODE = XMODE_RHS> struct X2SCfg {
   using C = typename CT<T>::type;
   using XC = X2Cfg<T, N>;
+  using G = X2SGroups<MODE>;
 #ifndef PSC_X2S_ROWS
 #define PSC_X2S_ROWS 6
 #endif
   static constexpr int M = KK + 1;
-  static constexpr int NA = 6, NB = 3;  // streams Y_UX..Y_DYUX, Y_PHI..Y_DZPHI
-#ifndef PSC_X2S_STAGE_B
-#define PSC_X2S_STAGE_B 1
-#endif
-  // stage the scalar streams too (else they are read from global memory)
-  static constexpr bool STAGE_B = PSC_X2S_STAGE_B;
   static constexpr unsigned ROW_BYTES = (unsigned)(M * sizeof(C));
-  static constexpr size_t STAGE_BYTES = (size_t)(NA + (STAGE_B ? NB : 0)) * ROW_BYTES;
+  static constexpr size_t STAGE_BYTES = (size_t)G::SLOTS * ROW_BYTES;
   static constexpr size_t GROUP_BYTES = STAGE_BYTES + XC::LINE_BYTES;
-  // rows in flight: PSC_X2S_ROWS, fewer where longer rows (the phase-shift
-  // sphere's cube) would not fit shared memory
+  // rows in flight: PSC_X2S_ROWS, fewer where longer rows (more streams, or the
+  // phase-shift sphere's cube) would not fit shared memory
   static constexpr int rows_fit() {
     int r = PSC_X2S_ROWS;
     while (r > 1 && GROUP_BYTES * r + XC::TW_BYTES + 2 * r * 8 > 227 * 1024) --r;
@@ -662,24 +686,25 @@ template <typename T, int N, int KK = (N - 1) / 3> struct X2SCfg {
   static constexpr size_t BAR_OFF = TW_OFF + XC::TW_BYTES;
   static constexpr size_t SMEM = BAR_OFF + 2 * ROWS * sizeof(unsigned long long);
   static constexpr bool OK = ROW_BYTES % 16 == 0 && SMEM <= 227 * 1024;
-  static_assert(Y_UX == 0 && Y_DYUX == NA - 1 && Y_PHI == NA && Y_DZPHI == NA + NB - 1,
-                "staged streams are contiguous");
+  static_assert((G::A & G::B) == 0 && (G::A | G::B) < (1u << G::SLOTS), "stream groups are disjoint slots");
 };
 
-template <typename T, int N, int KK = (N - 1) / 3, bool SHIFT = false>
-__global__ void __launch_bounds__(X2SCfg<T, N, KK>::THREADS, 1) k_xpass2s(PassArgs a) {
+template <typename T, int N, int KK = (N - 1) / 3, bool SHIFT = false, int MODE = XMODE_RHS>
+__global__ void __launch_bounds__(X2SCfg<T, N, KK, MODE>::THREADS, 1) k_xpass2s(PassArgs a) {
   using C = typename CT<T>::type;
   using XC = X2Cfg<T, N>;
-  using SC = X2SCfg<T, N, KK>;
+  using SC = X2SCfg<T, N, KK, MODE>;
+  using G = typename SC::G;
   static_assert(SC::OK, "staged x pass: rows must be 16-byte multiples and fit shared memory");
-  constexpr int TH = XC::TH, G = XC::G, ROWS = SC::ROWS, M = SC::M;
+  static_assert(MODE == XMODE_RHS || MODE == XMODE_CONVECTIVE, "staged x pass: right-hand side only");
+  constexpr int TH = XC::TH, G_ = XC::G, ROWS = SC::ROWS, M = SC::M;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int lid = threadIdx.x / TH;
   X2Roles<C> q;
   q.tid = threadIdx.x % TH;
-  q.ra = q.tid / G;
-  q.rr = q.tid % G;
-  q.rk0 = bitrev_lane<G>(q.rr);
+  q.ra = q.tid / G_;
+  q.rr = q.tid % G_;
+  q.rk0 = bitrev_lane<G_>(q.rr);
   q.bar = 1 + lid;
   unsigned char* grp = smraw + (size_t)lid * SC::GROUP_BYTES;
   C* stg = reinterpret_cast<C*>(grp);
@@ -704,12 +729,14 @@ __global__ void __launch_bounds__(X2SCfg<T, N, KK>::THREADS, 1) k_xpass2s(PassAr
   // row's wait runs out (every copy still lands)
   const unsigned long long lim = a.ctrl->wait_ns ? a.ctrl->wait_ns : 2000000000ull;
   bool stall = a.ctrl->stall_test != 0 && blockIdx.x == 0 && lid == 0;
-  // copies of streams [s0, s1) of row ln into the staging slots (one thread)
-  auto issue = [&](long long ln, int s0, int s1, unsigned long long* bar) {
+  // copies of the streams in `mask` of row ln into their staging slots (one thread)
+  auto issue = [&](long long ln, unsigned mask, unsigned long long* bar) {
     fence_proxy_async_smem();
-    mbar_expect_tx(bar, (unsigned)(s1 - s0) * SC::ROW_BYTES + (stall ? 16u : 0u));
+    mbar_expect_tx(bar, (unsigned)__popc(mask) * SC::ROW_BYTES + (stall ? 16u : 0u));
     stall = false;
-    for (int st = s0; st < s1; ++st) {
+#pragma unroll
+    for (int st = 0; st < G::SLOTS; ++st) {
+      if (!((mask >> st) & 1u)) continue;
       const long long src = st * ys + ln * M;
       if (PSC_OK_INDEX(src + M - 1, (long long)Y_NSTREAM * ys, a.ctrl))
         bulk_copy_g2s(stg + st * M, yb + src, SC::ROW_BYTES, bar);
@@ -722,11 +749,10 @@ __global__ void __launch_bounds__(X2SCfg<T, N, KK>::THREADS, 1) k_xpass2s(PassAr
   long long line = (long long)blockIdx.x * ROWS + lid;
   if (line < nlines) {
     if (leader) {
-      issue(line, 0, SC::NA, barA);
-      if constexpr (SC::STAGE_B) issue(line, SC::NA, SC::NA + SC::NB, barB);
+      issue(line, G::A, barA);
+      issue(line, G::B, barB);
     }
-    ia = true;
-    ib = SC::STAGE_B;
+    ia = ib = true;
   }
 #pragma unroll 1
   for (; line < nlines; line += stride) {
@@ -737,37 +763,33 @@ __global__ void __launch_bounds__(X2SCfg<T, N, KK>::THREADS, 1) k_xpass2s(PassAr
     if (!ok) break;
     pa ^= 1u;
     ia = false;
-    const C* __restrict__ row = yb + line * M;
-    auto Y = [&](int st, int kx) -> C {
-      if (SC::STAGE_B || st < SC::NA) return stg[st * M + kx];
-      return row[st * ys + kx];
+    auto Y = [&](int st, int kx) -> C { return stg[st * M + kx]; };
+    auto after_a = [&] {
+      if (next < nlines) {
+        if (leader) issue(next, G::A, barA);
+        ia = true;
+      }
     };
-    ok = x2_rhs_row<T, N, false, KK, SHIFT>(
-        Y,
-        [&] {
-          if (next < nlines) {
-            if (leader) issue(next, 0, SC::NA, barA);
-            ia = true;
-          }
-        },
-        [&] {
-          if constexpr (!SC::STAGE_B) return true;
-          const bool w = bar_and(q.bar, TH, leader ? mbar_wait(barB, pb, &a.ctrl->err, lim) : true);
-          if (w) {
-            pb ^= 1u;
-            ib = false;
-          }
-          return w;
-        },
-        [&] {
-          if constexpr (SC::STAGE_B) {
-            if (next < nlines) {
-              if (leader) issue(next, SC::NA, SC::NA + SC::NB, barB);
-              ib = true;
-            }
-          }
-        },
-        xb, line, ys, ex, q, scale, a.want_umax != 0, um, a.ctrl, a.phase);
+    auto wait_b = [&] {
+      const bool w = bar_and(q.bar, TH, leader ? mbar_wait(barB, pb, &a.ctrl->err, lim) : true);
+      if (w) {
+        pb ^= 1u;
+        ib = false;
+      }
+      return w;
+    };
+    auto after_b = [&] {
+      if (next < nlines) {
+        if (leader) issue(next, G::B, barB);
+        ib = true;
+      }
+    };
+    if constexpr (MODE == XMODE_RHS)
+      ok = x2_rhs_row<T, N, false, KK, SHIFT>(Y, after_a, wait_b, after_b, xb, line, ys, ex, q, scale,
+                                              a.want_umax != 0, um, a.ctrl, a.phase);
+    else
+      ok = x2_conv_row<T, N, KK, SHIFT>(Y, after_a, wait_b, after_b, xb, line, ys, ex, q, scale,
+                                        a.want_umax != 0, um, a.ctrl, a.phase);
     if (!ok) break;
   }
   if (!ok) {
